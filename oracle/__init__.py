@@ -1,0 +1,164 @@
+"""CPU oracle for the tremor-HMM likelihood -- test infrastructure only.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package. The product path (the CUDA library and
+its binding) never does, and the two share no code.
+
+The C source (``hmm_oracle.c``) is compiled with plain ``gcc -O2`` (no fast
+math) into ``_build/liboracle.so`` on first use, or by ``build()``.
+"""
+from __future__ import annotations
+
+import ctypes
+import hashlib
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = [_HERE / "hmm_oracle.c", _HERE / "mcmc_oracle.c"]
+_BUILD = _HERE / "_build"
+_lib = None
+
+
+def _digest() -> str:
+    h = hashlib.sha1()
+    for s in _SRC:
+        if s.exists():
+            h.update(s.read_bytes())
+    return h.hexdigest()[:12]
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle into a shared library (idempotent, keyed by source hash)."""
+    _BUILD.mkdir(exist_ok=True)
+    so = _BUILD / f"liboracle_{_digest()}.so"
+    if so.exists() and not force:
+        return so
+    srcs = [str(s) for s in _SRC if s.exists()]
+    tmp = so.with_suffix(f".tmp{os.getpid()}")
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
+           "-o", str(tmp), *srcs, "-lm", "-lpthread"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, so)
+    return so
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(str(build()))
+        _declare(_lib)
+    return _lib
+
+
+_f = ctypes.POINTER(ctypes.c_float)
+_d = ctypes.POINTER(ctypes.c_double)
+_u8 = ctypes.POINTER(ctypes.c_uint8)
+_i64 = ctypes.POINTER(ctypes.c_int64)
+_u32 = ctypes.POINTER(ctypes.c_uint32)
+_i32 = ctypes.POINTER(ctypes.c_int32)
+
+
+def _declare(L):
+    sig = [ctypes.c_int, _f, _f, _f, _f, _f, ctypes.c_int64, _f, _u8, ctypes.c_int]
+    for name in ("oracle_loglik", "oracle_loglik_backward", "oracle_loglik_ld",
+                 "oracle_loglik_bruteforce"):
+        fn = getattr(L, name)
+        fn.argtypes = sig
+        fn.restype = ctypes.c_double
+    L.oracle_log_emission.argtypes = [ctypes.c_int, _f, _f, _f, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_double, _d]
+    L.oracle_log_emission.restype = None
+    L.oracle_loglik_batched.argtypes = [ctypes.c_int, ctypes.c_int, _f, _f, _f, _f, _f,
+                                        ctypes.c_int, _i64, _f, _u8, ctypes.c_int, _d,
+                                        ctypes.c_int]
+    L.oracle_loglik_batched.restype = None
+    if hasattr(L, "oracle_philox4x32_10"):
+        _declare_mcmc(L)
+
+
+def _declare_mcmc(L):
+    L.oracle_philox4x32_10.argtypes = [_u32, _u32, _u32]
+    L.oracle_philox4x32_10.restype = None
+
+
+def compile_variant(source_text: str, out_dir) -> ctypes.CDLL:
+    """Compile a modified copy of the oracle source (mutation tests only)."""
+    out_dir = Path(out_dir)
+    src = out_dir / "variant.c"
+    src.write_text(source_text)
+    so = out_dir / "libvariant.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
+                    "-o", str(so), str(src), "-lm", "-lpthread"], check=True)
+    L = ctypes.CDLL(str(so))
+    _declare(L)
+    return L
+
+
+def _fp(a):
+    return a.ctypes.data_as(_f)
+
+
+def _c32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def _args(prm, xy, tremor):
+    pi, P, p, mu, cov = (_c32(x) for x in prm)
+    xy = _c32(xy).reshape(-1, 2)
+    tremor = np.ascontiguousarray(np.asarray(tremor, dtype=np.uint8))
+    keep = (pi, P, p, mu, cov, xy, tremor)
+    return keep, (int(pi.shape[-1]), _fp(pi), _fp(P), _fp(p), _fp(mu), _fp(cov),
+                  int(tremor.shape[0]), _fp(xy), tremor.ctypes.data_as(_u8))
+
+
+def _params(prm):
+    return prm.as_tuple() if hasattr(prm, "as_tuple") else tuple(prm)
+
+
+def loglik(prm, xy, tremor, init_mode: int = 0, _L=None) -> float:
+    """Scaled FP64 forward algorithm (Algorithm 1 with scale coefficients)."""
+    keep, a = _args(_params(prm), xy, tremor)
+    return (_L or lib()).oracle_loglik(*a, int(init_mode))
+
+
+def loglik_backward(prm, xy, tremor, init_mode: int = 0, _L=None) -> float:
+    keep, a = _args(_params(prm), xy, tremor)
+    return (_L or lib()).oracle_loglik_backward(*a, int(init_mode))
+
+
+def loglik_longdouble(prm, xy, tremor, init_mode: int = 0, _L=None) -> float:
+    keep, a = _args(_params(prm), xy, tremor)
+    return (_L or lib()).oracle_loglik_ld(*a, int(init_mode))
+
+
+def loglik_bruteforce(prm, xy, tremor, init_mode: int = 0, _L=None) -> float:
+    keep, a = _args(_params(prm), xy, tremor)
+    return (_L or lib()).oracle_loglik_bruteforce(*a, int(init_mode))
+
+
+def log_emission(prm, x: float, y: float, tremor: int, _L=None) -> np.ndarray:
+    pi, P, p, mu, cov = (_c32(x_) for x_ in _params(prm))
+    K = int(p.shape[0])
+    out = np.zeros(K, dtype=np.float64)
+    (_L or lib()).oracle_log_emission(K, _fp(p), _fp(mu), _fp(cov), int(tremor), float(x), float(y),
+                              out.ctypes.data_as(_d))
+    return out
+
+
+def loglik_batched(prm, xy, tremor, offsets, init_mode: int = 0, n_threads: int = 1) -> np.ndarray:
+    """Per-proposal sum over segments of log L; ``prm`` arrays are stacked [n_prop, ...]."""
+    pi, P, p, mu, cov = (_c32(x) for x in _params(prm))
+    n_prop, K = int(pi.shape[0]), int(pi.shape[1])
+    xy = _c32(xy).reshape(-1, 2)
+    tremor = np.ascontiguousarray(np.asarray(tremor, dtype=np.uint8))
+    offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    out = np.zeros(n_prop, dtype=np.float64)
+    lib().oracle_loglik_batched(n_prop, K, _fp(pi), _fp(P), _fp(p), _fp(mu), _fp(cov),
+                                int(offs.shape[0] - 1), offs.ctypes.data_as(_i64), _fp(xy),
+                                tremor.ctypes.data_as(_u8), int(init_mode),
+                                out.ctypes.data_as(_d), int(n_threads))
+    return out
