@@ -1,0 +1,344 @@
+"""Benchmark: batched tremor-HMM log-likelihood evaluations per second.
+
+Workload (one "step"): n_prop = 256 parameter proposals, each a random-walk
+perturbation of one generating parameter set, evaluated on one synthetic
+tremor-shaped sequence of T = 2^20 observations with K = 32 hidden states --
+one call of hmm_loglik_batched, i.e. every stage of the likelihood path
+(parameter constants, observation packing, chunk products, product tree,
+FP64 combine). Inputs are resident in HBM when the timed region starts; the
+L2 is flushed (a 256 MiB write) between timed steps, outside the events.
+
+Also reported on the same line:
+  plain_gpu     the same metric with the FP32-SIMT chunk products;
+  e2e           the same metric through hmm_loglik_batched_host (pinned host
+                buffers, host->device inputs and device->host results inside
+                the timed region);
+  roofline      the chunk-product kernel against its peak;
+  cpu_baseline  the FP64 CPU oracle on a bounded sample, on the host cores.
+
+``--impl reference`` times the CPU oracle instead (rank 0 only).
+Multi-GPU (torchrun): every rank evaluates its own n_prop proposals (weak
+scaling, no data-path collective); value = all ranks' evaluations / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "log-lik evals/s (K=32,T=2^20) batched TC vs plain GPU; ESS/s learned vs RW"
+UNIT = "evals/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="tf32")
+    ap.add_argument("--K", type=int, default=32)
+    ap.add_argument("--T", type=int, default=1 << 20)
+    ap.add_argument("--n-prop", type=int, default=256)
+    ap.add_argument("--chunk-len", type=int, default=0)
+    ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+# nominal dense tensor rates relative to bf16 (2.25 PF): tf32 1.1 PF
+NOMINAL_RATIO = {"tf32": 1.1 / 2.25, "tf32_split": 1.1 / 2.25, "bf16": 1.0}
+
+
+def roofline_peak(precision, pk):
+    d, src = pk
+    if precision == "fp32":
+        # 152 SMs x 128 FP32 lanes x 2 flop (FFMA) x max SM clock
+        mhz = float(d.get("sm_max_mhz", 2070.0))
+        return "alu", 152 * 128 * 2 * mhz * 1e6 / 1e12, f"derived: 152 SM x 128 FFMA x 2 x {mhz:.0f} MHz"
+    ratio = NOMINAL_RATIO[precision]
+    sus = float(d.get("bf16_tflops_sustained", d.get("bf16_tflops")))
+    return "tensor", sus * ratio, f"{src} bf16 sustained {sus} x nominal {precision}/bf16 ratio {ratio:.4f}"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.flush()
+        rows = []
+        with open(self.out.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.out.name)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(inputs, n_sample, cores):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    prm = inputs["params"]
+    sub = type(prm)(*(a[:n_sample] for a in prm.as_tuple()))
+    t0 = time.perf_counter()
+    oracle.loglik_batched(sub, inputs["xy"], inputs["tremor"], inputs["offsets"], n_threads=cores)
+    dt = time.perf_counter() - t0
+    return n_sample / dt, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2003_03508_gb300 import synth
+    cores = os.cpu_count() or 1
+    inputs = synth.batched_inputs(K=args.K, T=args.T, n_prop=cores, seed=args.seed)
+    for _ in range(args.warmup):
+        cpu_baseline(inputs, cores, cores)
+    times = []
+    for _ in range(args.steps):
+        _, dt = cpu_baseline(inputs, cores, cores)
+        times.append(dt)
+    ms = 1e3 * statistics.mean(times)
+    value = cores / (ms / 1e3)
+    sample = f"{cores} proposals x T={args.T} (K={args.K}) per step, one proposal per core"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"tremor HMM log-likelihood K={args.K} T={args.T} batched proposals",
+                   "K": args.K, "T": args.T},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    from paper_2003_03508_gb300 import api, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    inputs = synth.batched_inputs(K=args.K, T=args.T, n_prop=args.n_prop, seed=args.seed + 1000 * rank)
+    ctx = api.Context(local)
+    dev = api.to_device(inputs["params"])
+    xy = torch.from_numpy(inputs["xy"]).cuda()
+    fl = torch.from_numpy(inputs["tremor"]).cuda()
+    offs = inputs["offsets"]
+    opts = api.make_opts(precision=args.precision, chunk_len=args.chunk_len)
+    out = torch.empty(args.n_prop, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    steps_per_eval = int(offs[-1]) - (len(offs) - 1)
+    flops_per_eval = 2.0 * args.K ** 3 * steps_per_eval
+
+    def step():
+        ctx.hmm_loglik_batched(*dev, offs, xy, fl, opts=opts, out=out)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    launches_per_step = ctx.last_launch_count
+    L = ctx.last_chunk_len
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ctx.hmm_profile_enable(True)
+    barrier()
+    torch.cuda.synchronize()
+    evs = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    prof, ncalls = ctx.hmm_profile_read()
+    ctx.hmm_profile_enable(False)
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.n_prop * args.steps / (total_ms / 1e3)
+    status = ctx.hmm_status()
+
+    # roofline of the chunk-product kernel (its phase is one launch per step)
+    chunk_ms = prof["chunk"] / max(1, ncalls)
+    bound, peak, peak_src = roofline_peak(args.precision, peaks())
+    achieved = flops_per_eval * args.n_prop / (chunk_ms / 1e3) / 1e12
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "chunk_traffic.json")
+    if os.path.exists(tpath):
+        from paper_2003_03508_gb300 import build as _b
+        with open(tpath) as f:
+            tr = json.load(f)
+        key = f"{args.precision}:K{args.K}:T{args.T}:P{args.n_prop}"
+        ent = tr.get(key)
+        if ent and ent.get("build") == _b.library_path().stem:
+            traffic = ent["bytes_per_launch"]
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic, "kernel": "hmm chunk products",
+            "peak_source": peak_src, "kernel_ms": chunk_ms,
+            "phase_share": {k: v / max(1e-9, sum(prof.values())) for k, v in prof.items()}}
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": f"tremor HMM log-likelihood, K={args.K}, T={args.T}, "
+                               f"{args.n_prop} proposals batched per GPU",
+                   "K": args.K, "T": args.T, "n_prop": args.n_prop, "n_seg": len(offs) - 1,
+                   "precision": args.precision, "chunk_len": L,
+                   "l2": "flushed between timed steps (256 MiB write)"},
+        "roofline": roof,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "status": status,
+    }
+
+    # plain GPU (FP32-SIMT chunk products) on the same workload, fewer proposals
+    if not args.no_plain and args.precision != "fp32":
+        n_plain = min(args.n_prop, 32)
+        sub = tuple(t[:n_plain].contiguous() for t in dev)
+        po = api.make_opts(precision="fp32")
+        pout = torch.empty(n_plain, dtype=torch.float64, device="cuda")
+        ctx.hmm_loglik_batched(*sub, offs, xy, fl, opts=po, out=pout)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(2):
+            ctx.hmm_loglik_batched(*sub, offs, xy, fl, opts=po, out=pout)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1) / 2
+        result["plain_gpu"] = {"value": world * n_plain / (pms / 1e3), "unit": UNIT,
+                               "precision": "fp32_simt", "n_prop": n_plain, "ms_per_step": pms}
+        d = (out[:n_plain] - pout).abs().max().item()
+        result["plain_gpu"]["max_abs_diff_vs_tc"] = d
+
+    # end to end through the host-buffer entry point
+    if not args.no_e2e:
+        hp = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in inputs["params"].as_tuple()]
+        hxy = torch.from_numpy(inputs["xy"]).pin_memory()
+        hfl = torch.from_numpy(inputs["tremor"]).pin_memory()
+        hout = torch.empty(args.n_prop, dtype=torch.float64).pin_memory()
+        ctx.hmm_loglik_batched_host(*hp, offs, hxy, hfl, opts=opts, out=hout)
+        n_e2e = max(3, args.steps // 2)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n_e2e):
+            ctx.hmm_loglik_batched_host(*hp, offs, hxy, hfl, opts=opts, out=hout)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ems], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        h2d = sum(a.numel() * a.element_size() for a in hp) + hxy.numel() * 4 + hfl.numel()
+        result["e2e"] = {"value": world * args.n_prop * n_e2e / (ems / 1e3), "unit": UNIT,
+                         "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8 * args.n_prop,
+                         "steps": n_e2e, "ms_per_step": ems / n_e2e,
+                         "matches_device_result": bool(np.array_equal(hout.numpy(), out.cpu().numpy()))}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        n_sample = min(args.n_prop, cores)
+        v, dt = cpu_baseline(inputs, n_sample, cores)
+        result["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": min(cores, n_sample), "kind": "oracle",
+                                  "sample": f"{n_sample} of the {args.n_prop} proposals, full T={args.T}, "
+                                            f"one proposal per thread ({dt:.1f} s wall)"}
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result))
+
+
+if __name__ == "__main__":
+    main()

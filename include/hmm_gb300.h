@@ -1,0 +1,192 @@
+/*
+ * hmm_gb300.h -- C ABI of the GB300 (sm_103a) tremor-HMM likelihood library.
+ *
+ * What is computed (Section 2 of Stoltz et al., "A 1000-fold acceleration of
+ * hidden Markov model fitting using GPUs"):
+ *
+ *   Eq. "emission-matrix": for an observation o and hidden state k the
+ *   diagonal emission matrix D(o) has entries
+ *       D(o)_kk = p_k * phi(o | mu_k, Sigma_k)   if a tremor is observed at o in R^2,
+ *       D(o)_kk = 1 - p_k                         if no tremor is observed,
+ *   phi being the bivariate normal density.
+ *
+ *   Eq. "likelihood func": L = pi^T D_1 P D_2 P ... P D_T 1 (emit-first, the
+ *   default), or with HMM_INIT_TRANSITION_FIRST the printed form
+ *   L = pi^T P D_1 P D_2 ... P D_T 1. P (the paper's Gamma) is the transition
+ *   matrix, P[i*K+j] = Pr(i -> j); pi (the paper's delta) the initial vector.
+ *
+ *   Section "The likelihood algorithm", steps 1-3: the emissions are
+ *   evaluated in parallel, the matrices M_t = P D_t are multiplied as a chain
+ *   split into chunks, the chunk products are combined, and log L (not L) is
+ *   returned, with scale coefficients keeping every partial product in range.
+ *
+ * Conventions for every entry point:
+ *   - Every function returns an int status: HMM_OK (0) or one of HMM_E*.
+ *     Nothing traps or aborts; hmm_last_error() describes the last failure.
+ *   - Pointers are DEVICE pointers unless the name ends in _host. The caller
+ *     owns every buffer it passes; the library never frees or keeps them
+ *     past the call (results are written asynchronously on `stream`).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *   - K is 1..80. T (per segment) is >= 0; T = 0 gives log(sum_k pi_k).
+ *   - Parameter checks that need the device data (rows of P and pi >= 0 and
+ *     summing to 1 within 1e-5, 0 <= p_k <= 1, Sigma_k symmetric positive
+ *     definite, finite means, finite xy wherever a tremor is flagged) run on
+ *     the device: an invalid proposal's result is NaN and the context's
+ *     status word records HMM_EINVAL; hmm_status() synchronises and reads it.
+ *   - A true zero likelihood returns -INFINITY with HMM_OK.
+ *   - Results are bit-for-bit reproducible for the same inputs, options and
+ *     GPU model (fixed chunking, fixed reduction order, no atomics on data).
+ *   - One context per host thread; contexts are independent.
+ */
+#ifndef HMM_GB300_H
+#define HMM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define HMM_OK 0
+#define HMM_EINVAL 1       /* bad argument (host check) or bad parameter data (device check) */
+#define HMM_ECUDA 2        /* a CUDA runtime call failed; see hmm_last_error() */
+#define HMM_ENOMEM 3       /* workspace allocation failed */
+#define HMM_ENUMERIC 4     /* a value left the representable range (see hmm_status) */
+#define HMM_ETIMEOUT 5     /* a bounded device wait expired (kernel returned early) */
+#define HMM_EUNSUPPORTED 6 /* option not available for this K / device */
+
+/* ---- arithmetic of the chunk products (Step 3) ---- */
+#define HMM_PREC_FP32_SIMT 0  /* FP32 FFMA on the CUDA cores ("plain GPU") */
+#define HMM_PREC_TF32 1       /* tcgen05 tensor cores, TF32 operands, FP32 accumulation */
+#define HMM_PREC_BF16 2       /* tcgen05 tensor cores, BF16 running product, P as BF16 hi+lo */
+#define HMM_PREC_TF32_SPLIT 3 /* tcgen05 TF32 with P as TF32 hi+lo (two MMAs) */
+
+/* ---- where pi enters ---- */
+#define HMM_INIT_EMIT_FIRST 0       /* L = pi^T D_1 P D_2 ... (pi = law of the first state) */
+#define HMM_INIT_TRANSITION_FIRST 1 /* L = pi^T P D_1 P D_2 ... (Eq. "likelihood func", Algorithm 1) */
+
+typedef struct hmm_ctx hmm_ctx;
+
+/* One parameter set (Section 2: pi, P, and per state p_k, mu_k, Sigma_k). All float32, device. */
+typedef struct {
+    int32_t K;
+    const float *pi;       /* [K]                                        */
+    const float *P;        /* [K*K] row-major, P[i*K+j] = Pr(i -> j)      */
+    const float *p_tremor; /* [K]  probability of observing a tremor      */
+    const float *mu;       /* [K*2] (x, y) mean location                  */
+    const float *cov;      /* [K*3] (sxx, sxy, syy) covariance             */
+} hmm_params;
+
+/* One observation sequence x_0..x_{T-1} (Section 2: each is "no tremor" or a point in R^2). */
+typedef struct {
+    int64_t T;
+    const float *xy;        /* [T*2] (x, y); ignored where tremor == 0 */
+    const uint8_t *tremor;  /* [T]   1 = tremor observed at xy, 0 = none */
+} hmm_obs;
+
+typedef struct {
+    int32_t precision;    /* HMM_PREC_*                                           */
+    int32_t init_mode;    /* HMM_INIT_*                                           */
+    int32_t chunk_len;    /* steps per chunk product; 0 = chosen by the library   */
+    int32_t renorm_every; /* per-row power-of-two renormalisation interval; 0 = 4 */
+    int32_t recheck_fp32; /* batched: re-evaluate flagged proposals in FP32-SIMT   */
+    int32_t reserved[3];  /* must be 0                                             */
+} hmm_opts;
+
+/* Default options: FP32-SIMT, emit-first, automatic chunking, renorm every 4. */
+void hmm_opts_default(hmm_opts *opts);
+
+/* Create a context bound to CUDA device `device` (it becomes current on the calling thread). */
+int hmm_create(hmm_ctx **ctx, int device);
+
+/* Free the context's device workspace. NULL is accepted. */
+int hmm_destroy(hmm_ctx *ctx);
+
+/* Text of the last error on this context (never NULL). */
+const char *hmm_last_error(const hmm_ctx *ctx);
+
+/*
+ * Synchronise `stream`, read and clear the context's device status word.
+ * Returns HMM_OK, HMM_EINVAL (a parameter set or a flagged observation failed
+ * its checks), HMM_ENUMERIC or HMM_ETIMEOUT.
+ */
+int hmm_status(hmm_ctx *ctx, void *stream);
+
+/*
+ * log L for one parameter set and one sequence (Eq. "likelihood func",
+ * computed as Section "The likelihood algorithm" restructures it).
+ * out_dev: device pointer to one double.
+ */
+int hmm_loglik(hmm_ctx *ctx, const hmm_params *params, const hmm_obs *obs,
+               const hmm_opts *opts, double *out_dev, void *stream);
+
+/*
+ * Many proposals, many segments, one call (MCMC batch evaluation).
+ *   n_prop parameter sets, stacked: pi [n_prop*K], P [n_prop*K*K], p_tremor
+ *   [n_prop*K], mu [n_prop*K*2], cov [n_prop*K*3] (device).
+ *   n_seg independent observation segments, shared by every proposal:
+ *   segment s is xy/tremor[seg_offsets[s] .. seg_offsets[s+1]) and starts
+ *   from pi. seg_offsets is a HOST array of n_seg+1 non-decreasing int64,
+ *   seg_offsets[0] = 0.
+ *   out_dev[q] (device, n_prop doubles) = sum over s of log L(q | segment s),
+ *   summed in segment order.
+ */
+int hmm_loglik_batched(hmm_ctx *ctx, int32_t n_prop, int32_t K, const float *pi,
+                       const float *P, const float *p_tremor, const float *mu,
+                       const float *cov, int32_t n_seg, const int64_t *seg_offsets,
+                       const float *xy, const uint8_t *tremor, const hmm_opts *opts,
+                       double *out_dev, void *stream);
+
+/*
+ * hmm_loglik_batched with HOST buffers: copies the inputs into the context's
+ * device staging area on `stream`, evaluates, copies out_host[n_prop] back
+ * and synchronises `stream` before returning (pinned host memory makes the
+ * copies asynchronous up to that point). Returns the device status as
+ * hmm_status() would.
+ */
+int hmm_loglik_batched_host(hmm_ctx *ctx, int32_t n_prop, int32_t K, const float *pi,
+                            const float *P, const float *p_tremor, const float *mu,
+                            const float *cov, int32_t n_seg, const int64_t *seg_offsets,
+                            const float *xy, const uint8_t *tremor, const hmm_opts *opts,
+                            double *out_host, void *stream);
+
+/*
+ * Number of kernel launches the last hmm_loglik / hmm_loglik_batched call
+ * issued on its stream (for launch accounting in benchmarks).
+ */
+int hmm_last_launch_count(const hmm_ctx *ctx);
+
+/*
+ * Chunk length the last call used (after automatic selection).
+ */
+int hmm_last_chunk_len(const hmm_ctx *ctx);
+
+/* ---- per-phase device timing (benchmarks) ---- */
+#define HMM_PHASE_PREP 0   /* parameter checks and constants          */
+#define HMM_PHASE_PACK 1   /* observation packing                      */
+#define HMM_PHASE_CHUNK 2  /* chunk products (Section "Step 3")        */
+#define HMM_PHASE_TREE 3   /* combining the chunk products             */
+#define HMM_PHASE_FINAL 4  /* head vector, FP64 log L, segment sum     */
+#define HMM_PHASE_COUNT 5
+
+/*
+ * on != 0: every later call records CUDA events on its stream around each
+ * phase and accumulates the elapsed milliseconds (the event reads
+ * synchronise on those events at the start of the next call and in
+ * hmm_profile_read). on == 0: stop recording. Enabling resets the totals.
+ */
+int hmm_profile_enable(hmm_ctx *ctx, int on);
+
+/*
+ * Accumulated milliseconds per phase (ms_out[HMM_PHASE_COUNT]) and the number
+ * of calls recorded (*n_calls). Waits for the recorded events.
+ */
+int hmm_profile_read(hmm_ctx *ctx, double *ms_out, int *n_calls);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HMM_GB300_H */

@@ -1,0 +1,281 @@
+"""Python binding of the C ABI in ``include/hmm_gb300.h`` (argument marshalling only).
+
+Every function here checks shapes and dtypes, takes raw device pointers from
+torch tensors and calls the library; all arithmetic runs in the library's
+CUDA kernels. There is no CPU fallback: if the library cannot be built or
+loaded, or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+HMM_OK = 0
+HMM_EINVAL = 1
+HMM_ECUDA = 2
+HMM_ENOMEM = 3
+HMM_ENUMERIC = 4
+HMM_ETIMEOUT = 5
+HMM_EUNSUPPORTED = 6
+
+HMM_PREC_FP32_SIMT = 0
+HMM_PREC_TF32 = 1
+HMM_PREC_BF16 = 2
+HMM_PREC_TF32_SPLIT = 3
+
+HMM_INIT_EMIT_FIRST = 0
+HMM_INIT_TRANSITION_FIRST = 1
+
+PRECISIONS = {"fp32": HMM_PREC_FP32_SIMT, "tf32": HMM_PREC_TF32, "bf16": HMM_PREC_BF16,
+              "tf32_split": HMM_PREC_TF32_SPLIT}
+
+_ERR_NAMES = {1: "EINVAL", 2: "ECUDA", 3: "ENOMEM", 4: "ENUMERIC", 5: "ETIMEOUT", 6: "EUNSUPPORTED"}
+
+
+class HMMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"HMM_{_ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class hmm_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("init_mode", ctypes.c_int32),
+                ("chunk_len", ctypes.c_int32), ("renorm_every", ctypes.c_int32),
+                ("recheck_fp32", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class hmm_params(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("pi", ctypes.c_void_p), ("P", ctypes.c_void_p),
+                ("p_tremor", ctypes.c_void_p), ("mu", ctypes.c_void_p), ("cov", ctypes.c_void_p)]
+
+
+class hmm_obs(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int64), ("xy", ctypes.c_void_p), ("tremor", ctypes.c_void_p)]
+
+
+_lib = None
+_lib_lock = threading.Lock()
+
+_VP = ctypes.c_void_p
+_I32 = ctypes.c_int32
+
+# name -> (restype, argtypes); exactly the functions declared in include/hmm_gb300.h
+SIGNATURES = {
+    "hmm_opts_default": (None, [ctypes.POINTER(hmm_opts)]),
+    "hmm_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int]),
+    "hmm_destroy": (ctypes.c_int, [_VP]),
+    "hmm_last_error": (ctypes.c_char_p, [_VP]),
+    "hmm_status": (ctypes.c_int, [_VP, _VP]),
+    "hmm_loglik": (ctypes.c_int, [_VP, ctypes.POINTER(hmm_params), ctypes.POINTER(hmm_obs),
+                                  ctypes.POINTER(hmm_opts), _VP, _VP]),
+    "hmm_loglik_batched": (ctypes.c_int, [_VP, _I32, _I32, _VP, _VP, _VP, _VP, _VP, _I32, _VP,
+                                          _VP, _VP, ctypes.POINTER(hmm_opts), _VP, _VP]),
+    "hmm_loglik_batched_host": (ctypes.c_int, [_VP, _I32, _I32, _VP, _VP, _VP, _VP, _VP, _I32,
+                                               _VP, _VP, _VP, ctypes.POINTER(hmm_opts), _VP, _VP]),
+    "hmm_last_launch_count": (ctypes.c_int, [_VP]),
+    "hmm_last_chunk_len": (ctypes.c_int, [_VP]),
+    "hmm_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "hmm_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int)]),
+}
+
+PHASES = ("prep", "pack", "chunk", "tree", "final")
+
+
+def load_library(path=None) -> ctypes.CDLL:
+    """Build (if needed) and load the CUDA library; raises if that is impossible."""
+    global _lib
+    with _lib_lock:
+        if _lib is None or path is not None:
+            so = path or _build.build()
+            L = ctypes.CDLL(str(so))
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            if path is not None:
+                return L
+            _lib = L
+    return _lib
+
+
+def make_opts(precision="fp32", init_mode=HMM_INIT_EMIT_FIRST, chunk_len=0, renorm_every=0,
+              recheck_fp32=0) -> hmm_opts:
+    o = hmm_opts()
+    load_library().hmm_opts_default(ctypes.byref(o))
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.init_mode = int(init_mode)
+    o.chunk_len = int(chunk_len)
+    o.renorm_every = int(renorm_every)
+    o.recheck_fp32 = int(recheck_fp32)
+    return o
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _dev(t: torch.Tensor, dtype, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+class Context:
+    """Owns one ``hmm_ctx`` (workspace, plan cache, device status word)."""
+
+    def __init__(self, device: int | None = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the HMM library has no CPU path")
+        self.lib = load_library()
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        h = _VP()
+        rc = self.lib.hmm_create(ctypes.byref(h), self.device)
+        if rc != HMM_OK:
+            raise HMMError(rc, "hmm_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hmm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int):
+        if rc != HMM_OK:
+            raise HMMError(rc, self.lib.hmm_last_error(self.h).decode())
+
+    @property
+    def last_launch_count(self) -> int:
+        return int(self.lib.hmm_last_launch_count(self.h))
+
+    @property
+    def last_chunk_len(self) -> int:
+        return int(self.lib.hmm_last_chunk_len(self.h))
+
+    def hmm_profile_enable(self, on: bool = True):
+        self._check(self.lib.hmm_profile_enable(self.h, int(bool(on))))
+
+    def hmm_profile_read(self):
+        """(dict phase -> accumulated ms, number of recorded calls)."""
+        ms = (ctypes.c_double * len(PHASES))()
+        n = ctypes.c_int()
+        self._check(self.lib.hmm_profile_read(self.h, ms, ctypes.byref(n)))
+        return dict(zip(PHASES, list(ms))), int(n.value)
+
+    def hmm_status(self, stream=None) -> int:
+        """Synchronise, read and clear the device status word (returns the code)."""
+        return int(self.lib.hmm_status(self.h, _stream_ptr(stream)))
+
+    def hmm_loglik(self, pi, P, p_tremor, mu, cov, xy, tremor, opts=None, out=None, stream=None):
+        """log L of one parameter set on one sequence; returns a float64 [1] CUDA tensor."""
+        K = int(pi.shape[0])
+        for t, n in ((pi, "pi"), (P, "P"), (p_tremor, "p_tremor"), (mu, "mu"), (cov, "cov")):
+            _dev(t, torch.float32, n)
+        _dev(xy, torch.float32, "xy")
+        _dev(tremor, torch.uint8, "tremor")
+        T = int(tremor.shape[0])
+        if out is None:
+            out = torch.empty(1, dtype=torch.float64, device=pi.device)
+        prm = hmm_params(K, pi.data_ptr(), P.data_ptr(), p_tremor.data_ptr(), mu.data_ptr(),
+                         cov.data_ptr())
+        ob = hmm_obs(T, xy.data_ptr() if T else None, tremor.data_ptr() if T else None)
+        o = opts if opts is not None else make_opts()
+        self._check(self.lib.hmm_loglik(self.h, ctypes.byref(prm), ctypes.byref(ob),
+                                        ctypes.byref(o), out.data_ptr(), _stream_ptr(stream)))
+        return out
+
+    def hmm_loglik_batched(self, pi, P, p_tremor, mu, cov, seg_offsets, xy, tremor, opts=None,
+                           out=None, stream=None):
+        """Per-proposal sum over segments of log L (float64 [n_prop] CUDA tensor)."""
+        n_prop, K = int(pi.shape[0]), int(pi.shape[1])
+        for t, n in ((pi, "pi"), (P, "P"), (p_tremor, "p_tremor"), (mu, "mu"), (cov, "cov")):
+            _dev(t, torch.float32, n)
+        _dev(xy, torch.float32, "xy")
+        _dev(tremor, torch.uint8, "tremor")
+        offs = np.ascontiguousarray(np.asarray(seg_offsets, dtype=np.int64))
+        if out is None:
+            out = torch.empty(n_prop, dtype=torch.float64, device=pi.device)
+        o = opts if opts is not None else make_opts()
+        T = int(offs[-1])
+        self._check(self.lib.hmm_loglik_batched(
+            self.h, n_prop, K, pi.data_ptr(), P.data_ptr(), p_tremor.data_ptr(), mu.data_ptr(),
+            cov.data_ptr(), int(offs.shape[0] - 1), offs.ctypes.data,
+            xy.data_ptr() if T else None, tremor.data_ptr() if T else None, ctypes.byref(o),
+            out.data_ptr(), _stream_ptr(stream)))
+        return out
+
+    def hmm_loglik_batched_host(self, pi, P, p_tremor, mu, cov, seg_offsets, xy, tremor,
+                                opts=None, out=None, stream=None):
+        """Same as hmm_loglik_batched, with host (numpy or CPU-tensor) inputs and output."""
+        def host(a, dt):
+            if isinstance(a, torch.Tensor):
+                if a.is_cuda:
+                    raise TypeError("host entry point takes host buffers")
+                if not a.is_contiguous():
+                    raise ValueError("host buffers must be contiguous")
+                return a, a.data_ptr()
+            a = np.ascontiguousarray(a, dtype=dt)
+            return a, a.ctypes.data
+        keep = []
+        ptrs = []
+        for a, dt in ((pi, np.float32), (P, np.float32), (p_tremor, np.float32), (mu, np.float32),
+                      (cov, np.float32), (xy, np.float32), (tremor, np.uint8)):
+            k, ptr = host(a, dt)
+            keep.append(k)
+            ptrs.append(ptr)
+        n_prop, K = int(keep[0].shape[0]), int(keep[0].shape[1])
+        offs = np.ascontiguousarray(np.asarray(seg_offsets, dtype=np.int64))
+        if out is None:
+            out = np.empty(n_prop, dtype=np.float64)
+        optr = out.data_ptr() if isinstance(out, torch.Tensor) else out.ctypes.data
+        o = opts if opts is not None else make_opts()
+        self._check(self.lib.hmm_loglik_batched_host(
+            self.h, n_prop, K, *ptrs[:5], int(offs.shape[0] - 1), offs.ctypes.data, ptrs[5],
+            ptrs[6], ctypes.byref(o), optr, _stream_ptr(stream)))
+        return out
+
+
+_default_ctx = {}
+
+
+def default_context() -> Context:
+    dev = torch.cuda.current_device()
+    if dev not in _default_ctx:
+        _default_ctx[dev] = Context(dev)
+    return _default_ctx[dev]
+
+
+def hmm_loglik(*args, **kw):
+    return default_context().hmm_loglik(*args, **kw)
+
+
+def hmm_loglik_batched(*args, **kw):
+    return default_context().hmm_loglik_batched(*args, **kw)
+
+
+def hmm_loglik_batched_host(*args, **kw):
+    return default_context().hmm_loglik_batched_host(*args, **kw)
+
+
+def to_device(prm, device="cuda"):
+    """HMMParams (numpy) -> tuple of CUDA float32 tensors (pi, P, p_tremor, mu, cov)."""
+    return tuple(torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(device)
+                 for a in prm.as_tuple())

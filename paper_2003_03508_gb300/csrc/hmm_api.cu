@@ -1,0 +1,526 @@
+// C ABI: context, workspace, planning and the launch sequence.
+//
+// One call of hmm_loglik_batched is (Section "The likelihood algorithm"):
+//   prep   -> per-proposal constants (and parameter checks)
+//   pack   -> observations into 64-step aligned windows
+//   chunk  -> every chunk's product of P D_t (steps 1-3, fused)
+//   tree   -> ordered products of the chunk products, level by level
+//   final  -> head vector pi0 D_0 times the product, log L in FP64, summed
+//             over segments in order
+// Every launch goes to the caller's stream; nothing synchronises unless the
+// caller asks (hmm_status, or the _host entry point).
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "hmm_internal.cuh"
+
+using namespace hmm;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+struct Plan {
+    bool valid = false;
+    int K = 0, n_prop = 0, n_seg = 0, precision = -1, L = 0;
+    std::vector<int64_t> offsets;
+    // derived
+    ConstLayout lay{};
+    int64_t n_packed = 0;
+    int n_chunks = 0;
+    int n_levels = 0;  // number of tree levels that run (level l -> l+1)
+    std::vector<int32_t> level_n;           // matrices per proposal at each level
+    std::vector<std::vector<TreeGroup>> groups;
+    std::vector<SegFinal> segfinal;
+    std::vector<int64_t> pbase;
+    std::vector<ChunkDesc> chunks;
+    // device copies (inside plan_buf)
+    ChunkDesc *d_chunks = nullptr;
+    TreeGroup *d_groups[MAX_LEVELS] = {};
+    SegFinal *d_segs = nullptr;
+    int64_t *d_offsets = nullptr;
+    int64_t *d_pbase = nullptr;
+};
+
+}  // namespace
+
+struct hmm_ctx {
+    int device = 0;
+    char err[512] = {0};
+    DevBuf work;       // per-call workspace
+    DevBuf planbuf;    // plan tables
+    DevBuf stage;      // staging area for the _host entry point
+    unsigned *d_status = nullptr;
+    Plan plan;
+    int last_launches = 0;
+    int last_L = 0;
+    // phase timing
+    bool prof_on = false;
+    bool prof_pending = false;
+    cudaEvent_t ev[HMM_PHASE_COUNT + 1] = {};
+    double prof_ms[HMM_PHASE_COUNT] = {};
+    int prof_calls = 0;
+};
+
+// fold the events of the previous recorded call into the totals
+static void prof_collect(hmm_ctx *c) {
+    if (!c->prof_pending) return;
+    cudaEventSynchronize(c->ev[HMM_PHASE_COUNT]);
+    for (int i = 0; i < HMM_PHASE_COUNT; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]) == cudaSuccess) c->prof_ms[i] += ms;
+    }
+    cudaGetLastError();
+    c->prof_calls += 1;
+    c->prof_pending = false;
+}
+
+static void prof_mark(hmm_ctx *c, int i, cudaStream_t st) {
+    if (c->prof_on) cudaEventRecord(c->ev[i], st);
+}
+
+static int fail(hmm_ctx *c, int code, const char *fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+static int cuda_fail(hmm_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, HMM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static int ensure(hmm_ctx *c, DevBuf &b, size_t bytes) {
+    if (b.cap >= bytes) return HMM_OK;
+    if (b.p) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaDeviceSynchronize");
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    size_t want = bytes + bytes / 8 + 4096;
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return fail(c, HMM_ENOMEM, "cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
+    }
+    b.cap = want;
+    return HMM_OK;
+}
+
+// simple bump carve of an existing buffer
+struct Carve {
+    char *base;
+    size_t off = 0;
+    explicit Carve(void *b) : base((char *)b) {}
+    template <class T>
+    T *take(size_t n) {
+        off = (off + 255) & ~(size_t)255;
+        T *r = (T *)(base + off);
+        off += n * sizeof(T);
+        return r;
+    }
+};
+
+static int choose_chunk_len(int precision, int n_prop, int KP, int64_t steps_total) {
+    // enough independent rows to fill the GPU a few times over, chunk length
+    // a multiple of the 64-step observation window
+    double rows_target = precision == HMM_PREC_FP32_SIMT ? 152.0 * 2048.0 : 152.0 * 1024.0;
+    double chunks_target = rows_target / ((double)n_prop * KP);
+    if (chunks_target < 1.0) chunks_target = 1.0;
+    double L = (double)steps_total / chunks_target;
+    int64_t Li = ((int64_t)L + 63) / 64 * 64;
+    if (Li < 64) Li = 64;
+    if (Li > 16384) Li = 16384;
+    return (int)Li;
+}
+
+static void build_plan(Plan &pl, int K, int n_prop, int n_seg, const int64_t *offs, int precision,
+                       int L) {
+    pl.K = K;
+    pl.n_prop = n_prop;
+    pl.n_seg = n_seg;
+    pl.precision = precision;
+    pl.L = L;
+    pl.offsets.assign(offs, offs + n_seg + 1);
+    pl.lay = make_layout(K, precision);
+    pl.pbase.assign(n_seg, 0);
+    pl.chunks.clear();
+    std::vector<int> C(n_seg), first(n_seg);
+    int64_t pb = 0;
+    for (int s = 0; s < n_seg; ++s) {
+        int64_t T = offs[s + 1] - offs[s];
+        int64_t steps = T > 1 ? T - 1 : 0;
+        pl.pbase[s] = pb;
+        pb += (steps + OBS_WIN - 1) / OBS_WIN * OBS_WIN;
+        C[s] = (int)((steps + L - 1) / L);
+        first[s] = (int)pl.chunks.size();
+        for (int c = 0; c < C[s]; ++c) {
+            ChunkDesc d;
+            d.pstart = pl.pbase[s] + (int64_t)c * L;
+            d.len = (int)std::min<int64_t>(L, steps - (int64_t)c * L);
+            d.seg = s;
+            pl.chunks.push_back(d);
+        }
+    }
+    pl.n_packed = pb > 0 ? pb : OBS_WIN;
+    pl.n_chunks = (int)pl.chunks.size();
+    // tree levels
+    pl.level_n.assign(1, pl.n_chunks);
+    pl.groups.clear();
+    pl.segfinal.assign(n_seg, SegFinal{});
+    std::vector<int> cnt(C), base(first);
+    for (int s = 0; s < n_seg; ++s) {
+        pl.segfinal[s].T = offs[s + 1] - offs[s];
+        pl.segfinal[s].level = cnt[s] >= 1 ? 0 : -1;
+        pl.segfinal[s].idx = base[s];
+    }
+    int level = 0;
+    for (;;) {
+        bool any = false;
+        for (int s = 0; s < n_seg; ++s) any = any || cnt[s] > 1;
+        if (!any) break;
+        std::vector<TreeGroup> gs;
+        int nout = 0;
+        for (int s = 0; s < n_seg; ++s) {
+            if (cnt[s] <= 1) continue;
+            int ng = (cnt[s] + TREE_GROUP - 1) / TREE_GROUP;
+            for (int g = 0; g < ng; ++g) {
+                TreeGroup tg;
+                tg.src = base[s] + g * TREE_GROUP;
+                tg.cnt = std::min(TREE_GROUP, cnt[s] - g * TREE_GROUP);
+                tg.dst = nout + g;
+                tg.pad = 0;
+                gs.push_back(tg);
+            }
+            base[s] = nout;
+            cnt[s] = ng;
+            nout += ng;
+            pl.segfinal[s].level = level + 1;
+            pl.segfinal[s].idx = base[s];
+        }
+        pl.groups.push_back(gs);
+        pl.level_n.push_back(nout);
+        ++level;
+    }
+    pl.n_levels = level;
+    pl.valid = true;
+}
+
+static bool plan_matches(const Plan &pl, int K, int n_prop, int n_seg, const int64_t *offs,
+                         int precision, int L) {
+    if (!pl.valid || pl.K != K || pl.n_prop != n_prop || pl.n_seg != n_seg ||
+        pl.precision != precision || pl.L != L)
+        return false;
+    return std::equal(pl.offsets.begin(), pl.offsets.end(), offs);
+}
+
+static int upload_plan(hmm_ctx *c, cudaStream_t st) {
+    Plan &pl = c->plan;
+    size_t bytes = 0;
+    auto add = [&](size_t b) { bytes += (b + 255) & ~(size_t)255; };
+    add(sizeof(ChunkDesc) * std::max<size_t>(1, pl.chunks.size()));
+    for (auto &g : pl.groups) add(sizeof(TreeGroup) * std::max<size_t>(1, g.size()));
+    add(sizeof(SegFinal) * pl.segfinal.size());
+    add(sizeof(int64_t) * pl.offsets.size());
+    add(sizeof(int64_t) * pl.pbase.size());
+    int rc = ensure(c, c->planbuf, bytes + 4096);
+    if (rc) return rc;
+    Carve cv(c->planbuf.p);
+    pl.d_chunks = cv.take<ChunkDesc>(std::max<size_t>(1, pl.chunks.size()));
+    for (int l = 0; l < pl.n_levels; ++l) pl.d_groups[l] = cv.take<TreeGroup>(std::max<size_t>(1, pl.groups[l].size()));
+    pl.d_segs = cv.take<SegFinal>(pl.segfinal.size());
+    pl.d_offsets = cv.take<int64_t>(pl.offsets.size());
+    pl.d_pbase = cv.take<int64_t>(pl.pbase.size());
+    cudaError_t e = cudaSuccess;
+    if (!pl.chunks.empty())
+        e = cudaMemcpyAsync(pl.d_chunks, pl.chunks.data(), sizeof(ChunkDesc) * pl.chunks.size(), cudaMemcpyHostToDevice, st);
+    for (int l = 0; l < pl.n_levels && e == cudaSuccess; ++l)
+        e = cudaMemcpyAsync(pl.d_groups[l], pl.groups[l].data(), sizeof(TreeGroup) * pl.groups[l].size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(pl.d_segs, pl.segfinal.data(), sizeof(SegFinal) * pl.segfinal.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(pl.d_offsets, pl.offsets.data(), sizeof(int64_t) * pl.offsets.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(pl.d_pbase, pl.pbase.data(), sizeof(int64_t) * pl.pbase.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host vectors may change after return
+    if (e != cudaSuccess) {
+        pl.valid = false;
+        return cuda_fail(c, e, "plan upload");
+    }
+    return HMM_OK;
+}
+
+extern "C" {
+
+void hmm_opts_default(hmm_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->precision = HMM_PREC_FP32_SIMT;
+    o->init_mode = HMM_INIT_EMIT_FIRST;
+    o->chunk_len = 0;
+    o->renorm_every = 0;
+}
+
+int hmm_create(hmm_ctx **out, int device) {
+    if (!out) return HMM_EINVAL;
+    *out = nullptr;
+    hmm_ctx *c = new (std::nothrow) hmm_ctx();
+    if (!c) return HMM_ENOMEM;
+    c->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(unsigned));
+    if (e != cudaSuccess) {
+        int rc = e == cudaErrorMemoryAllocation ? HMM_ENOMEM : HMM_ECUDA;
+        cudaGetLastError();
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return HMM_OK;
+}
+
+int hmm_destroy(hmm_ctx *c) {
+    if (!c) return HMM_OK;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    if (c->work.p) cudaFree(c->work.p);
+    if (c->planbuf.p) cudaFree(c->planbuf.p);
+    if (c->stage.p) cudaFree(c->stage.p);
+    if (c->d_status) cudaFree(c->d_status);
+    for (auto &e : c->ev)
+        if (e) cudaEventDestroy(e);
+    delete c;
+    return HMM_OK;
+}
+
+const char *hmm_last_error(const hmm_ctx *c) { return c ? c->err : "null context"; }
+
+int hmm_last_launch_count(const hmm_ctx *c) { return c ? c->last_launches : -1; }
+
+int hmm_last_chunk_len(const hmm_ctx *c) { return c ? c->last_L : -1; }
+
+int hmm_profile_enable(hmm_ctx *c, int on) {
+    if (!c) return HMM_EINVAL;
+    cudaSetDevice(c->device);
+    prof_collect(c);
+    if (on && !c->ev[0]) {
+        for (auto &e : c->ev) {
+            cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) return cuda_fail(c, r, "cudaEventCreate");
+        }
+    }
+    c->prof_on = on != 0;
+    if (on) {
+        for (double &m : c->prof_ms) m = 0.0;
+        c->prof_calls = 0;
+    }
+    return HMM_OK;
+}
+
+int hmm_profile_read(hmm_ctx *c, double *ms_out, int *n_calls) {
+    if (!c || !ms_out) return HMM_EINVAL;
+    cudaSetDevice(c->device);
+    prof_collect(c);
+    for (int i = 0; i < HMM_PHASE_COUNT; ++i) ms_out[i] = c->prof_ms[i];
+    if (n_calls) *n_calls = c->prof_calls;
+    return HMM_OK;
+}
+
+int hmm_status(hmm_ctx *c, void *stream) {
+    if (!c) return HMM_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "hmm_status");
+    if (h & ST_EINVAL) return fail(c, HMM_EINVAL, "a parameter set or a flagged observation failed its checks");
+    if (h & ST_ENUMERIC) return fail(c, HMM_ENUMERIC, "a scaled value left the representable range");
+    if (h & ST_ETIMEOUT) return fail(c, HMM_ETIMEOUT, "a bounded device wait expired");
+    return HMM_OK;
+}
+
+int hmm_loglik_batched(hmm_ctx *c, int32_t n_prop, int32_t K, const float *pi, const float *P,
+                       const float *p, const float *mu, const float *cov, int32_t n_seg,
+                       const int64_t *offs, const float *xy, const uint8_t *tremor,
+                       const hmm_opts *opts_in, double *out, void *stream) {
+    if (!c) return HMM_EINVAL;
+    c->last_launches = 0;
+    hmm_opts opts;
+    if (opts_in) opts = *opts_in; else hmm_opts_default(&opts);
+    if (K < 1 || K > 80) return fail(c, HMM_EINVAL, "K=%d outside 1..80", K);
+    if (n_prop < 1) return fail(c, HMM_EINVAL, "n_prop=%d < 1", n_prop);
+    if (n_seg < 1 || !offs) return fail(c, HMM_EINVAL, "need n_seg >= 1 and seg_offsets");
+    if (!pi || !P || !p || !mu || !cov || !out) return fail(c, HMM_EINVAL, "null parameter or output pointer");
+    if (offs[0] != 0) return fail(c, HMM_EINVAL, "seg_offsets[0] must be 0");
+    for (int s = 0; s < n_seg; ++s)
+        if (offs[s + 1] < offs[s]) return fail(c, HMM_EINVAL, "seg_offsets must be non-decreasing");
+    const int64_t T_total = offs[n_seg];
+    if (T_total > 0 && (!xy || !tremor)) return fail(c, HMM_EINVAL, "null observation pointer");
+    if (xy && ((uintptr_t)xy & 7)) return fail(c, HMM_EINVAL, "xy must be 8-byte aligned");
+    if (opts.init_mode != HMM_INIT_EMIT_FIRST && opts.init_mode != HMM_INIT_TRANSITION_FIRST)
+        return fail(c, HMM_EINVAL, "bad init_mode %d", opts.init_mode);
+    if (opts.chunk_len < 0 || (opts.chunk_len % OBS_WIN) != 0)
+        return fail(c, HMM_EINVAL, "chunk_len must be 0 or a positive multiple of %d", OBS_WIN);
+    if (opts.renorm_every < 0 || opts.renorm_every > 64)
+        return fail(c, HMM_EINVAL, "renorm_every must be 0..64");
+    for (int r = 0; r < 3; ++r)
+        if (opts.reserved[r]) return fail(c, HMM_EINVAL, "reserved option fields must be 0");
+    const int prec = opts.precision;
+    if (prec != HMM_PREC_FP32_SIMT && prec != HMM_PREC_TF32 && prec != HMM_PREC_BF16 &&
+        prec != HMM_PREC_TF32_SPLIT)
+        return fail(c, HMM_EINVAL, "bad precision %d", prec);
+    if (prec != HMM_PREC_FP32_SIMT && !chunk_tc_supported(K, prec))
+        return fail(c, HMM_EUNSUPPORTED, "tensor-core path does not support K=%d precision %d", K, prec);
+    const int renorm = opts.renorm_every ? opts.renorm_every : 4;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+
+    // ---- plan (cached while the shape is unchanged) ----
+    ConstLayout lay = make_layout(K, prec);
+    int64_t steps_total = 0;
+    for (int s = 0; s < n_seg; ++s) steps_total += std::max<int64_t>(0, offs[s + 1] - offs[s] - 1);
+    int L = opts.chunk_len ? opts.chunk_len : choose_chunk_len(prec, n_prop, lay.KP, steps_total);
+    if (!plan_matches(c->plan, K, n_prop, n_seg, offs, prec, L)) {
+        build_plan(c->plan, K, n_prop, n_seg, offs, prec, L);
+        if (c->plan.n_levels + 1 > MAX_LEVELS) {
+            c->plan.valid = false;
+            return fail(c, HMM_EINVAL, "too many chunks for the tree (raise chunk_len)");
+        }
+        int rc = upload_plan(c, st);
+        if (rc) return rc;
+    }
+    Plan &pl = c->plan;
+    c->last_L = L;
+
+    // ---- workspace ----
+    const int KP = lay.KP;
+    size_t need = 0;
+    auto add = [&](size_t b) { need += (b + 255) & ~(size_t)255; };
+    add(sizeof(float) * (size_t)n_prop * lay.stride);
+    add(sizeof(int) * (size_t)n_prop);
+    add(sizeof(int));
+    add(sizeof(float2) * (size_t)pl.n_packed);
+    add(sizeof(float2) * (size_t)n_seg);
+    for (int l = 0; l <= pl.n_levels; ++l) {
+        add(sizeof(float) * (size_t)n_prop * std::max(1, pl.level_n[l]) * KP * KP);
+        add((l == 0 ? 4 : 8) * (size_t)n_prop * std::max(1, pl.level_n[l]) * KP);
+    }
+    int rc = ensure(c, c->work, need + 4096);
+    if (rc) return rc;
+    Carve cv(c->work.p);
+    float *cblock = cv.take<float>((size_t)n_prop * lay.stride);
+    int *prop_bad = cv.take<int>(n_prop);
+    int *obs_bad = cv.take<int>(1);
+    float2 *packed = cv.take<float2>(pl.n_packed);
+    float2 *head = cv.take<float2>(n_seg);
+    LevelPtrs lv{};
+    for (int l = 0; l <= pl.n_levels; ++l) {
+        lv.A[l] = cv.take<float>((size_t)n_prop * std::max(1, pl.level_n[l]) * KP * KP);
+        if (l == 0) lv.e[l] = cv.take<int32_t>((size_t)n_prop * std::max(1, pl.level_n[l]) * KP);
+        else lv.e[l] = cv.take<long long>((size_t)n_prop * std::max(1, pl.level_n[l]) * KP);
+        lv.n[l] = pl.level_n[l];
+    }
+
+    // ---- launches ----
+    int launches = 0;
+    prof_collect(c);
+    prof_mark(c, HMM_PHASE_PREP, st);
+    e = cudaMemsetAsync(obs_bad, 0, sizeof(int), st);
+    if (e == cudaSuccess) { e = launch_prep(n_prop, K, lay, prec, opts.init_mode, pi, P, p, mu, cov, cblock, prop_bad, c->d_status, st); ++launches; }
+    prof_mark(c, HMM_PHASE_PACK, st);
+    if (e == cudaSuccess && T_total > 0) { e = launch_pack(n_seg, pl.d_offsets, pl.d_pbase, T_total, xy, tremor, packed, head, obs_bad, c->d_status, st); ++launches; }
+    prof_mark(c, HMM_PHASE_CHUNK, st);
+    if (e == cudaSuccess && pl.n_chunks > 0) {
+        if (prec == HMM_PREC_FP32_SIMT)
+            e = launch_chunk_simt(n_prop, pl.n_chunks, L, renorm, lay, cblock, pl.d_chunks, packed, lv.A[0], (int32_t *)lv.e[0], c->d_status, st);
+        else
+            e = launch_chunk_tc(n_prop, pl.n_chunks, L, renorm, prec, lay, cblock, pl.d_chunks, packed, lv.A[0], (int32_t *)lv.e[0], c->d_status, st);
+        ++launches;
+    }
+    prof_mark(c, HMM_PHASE_TREE, st);
+    for (int l = 0; l < pl.n_levels && e == cudaSuccess; ++l) {
+        e = launch_tree_level(n_prop, KP, l, (int)pl.groups[l].size(), pl.d_groups[l], lv, c->d_status, st);
+        ++launches;
+    }
+    prof_mark(c, HMM_PHASE_FINAL, st);
+    if (e == cudaSuccess) {
+        e = launch_final(n_prop, K, opts.init_mode, n_seg, pl.d_segs, head, lv, KP, pi, P, p, mu, cov, prop_bad, obs_bad, out, st);
+        ++launches;
+    }
+    prof_mark(c, HMM_PHASE_COUNT, st);
+    if (c->prof_on) c->prof_pending = true;
+    c->last_launches = launches;
+    if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+    return HMM_OK;
+}
+
+int hmm_loglik(hmm_ctx *c, const hmm_params *prm, const hmm_obs *obs, const hmm_opts *opts,
+               double *out, void *stream) {
+    if (!c) return HMM_EINVAL;
+    if (!prm || !obs) return fail(c, HMM_EINVAL, "null params or obs");
+    if (obs->T < 0) return fail(c, HMM_EINVAL, "T < 0");
+    int64_t offs[2] = {0, obs->T};
+    return hmm_loglik_batched(c, 1, prm->K, prm->pi, prm->P, prm->p_tremor, prm->mu, prm->cov, 1,
+                              offs, obs->xy, obs->tremor, opts, out, stream);
+}
+
+int hmm_loglik_batched_host(hmm_ctx *c, int32_t n_prop, int32_t K, const float *pi, const float *P,
+                            const float *p, const float *mu, const float *cov, int32_t n_seg,
+                            const int64_t *offs, const float *xy, const uint8_t *tremor,
+                            const hmm_opts *opts, double *out_host, void *stream) {
+    if (!c) return HMM_EINVAL;
+    if (K < 1 || K > 80 || n_prop < 1 || n_seg < 1 || !offs || !out_host || !pi || !P || !p || !mu || !cov)
+        return fail(c, HMM_EINVAL, "bad arguments");
+    const int64_t T_total = offs[n_seg];
+    if (T_total < 0) return fail(c, HMM_EINVAL, "bad seg_offsets");
+    if (T_total > 0 && (!xy || !tremor)) return fail(c, HMM_EINVAL, "null observation pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    const size_t nk = (size_t)n_prop * K;
+    size_t need = 0;
+    auto add = [&](size_t b) { need += (b + 255) & ~(size_t)255; };
+    add(4 * nk); add(4 * nk * K); add(4 * nk); add(8 * nk); add(12 * nk);
+    add(8 * (size_t)T_total); add((size_t)T_total); add(8 * (size_t)n_prop);
+    int rc = ensure(c, c->stage, need + 4096);
+    if (rc) return rc;
+    Carve cv(c->stage.p);
+    float *dpi = cv.take<float>(nk), *dP = cv.take<float>(nk * K), *dp = cv.take<float>(nk);
+    float *dmu = cv.take<float>(2 * nk), *dcov = cv.take<float>(3 * nk);
+    float *dxy = cv.take<float>(2 * (size_t)T_total);
+    uint8_t *dtr = cv.take<uint8_t>((size_t)T_total);
+    double *dout = cv.take<double>(n_prop);
+    struct { void *d; const void *h; size_t n; } cp[] = {
+        {dpi, pi, 4 * nk}, {dP, P, 4 * nk * K}, {dp, p, 4 * nk}, {dmu, mu, 8 * nk},
+        {dcov, cov, 12 * nk}, {dxy, xy, 8 * (size_t)T_total}, {dtr, tremor, (size_t)T_total}};
+    for (auto &x : cp) {
+        if (x.n == 0) continue;
+        e = cudaMemcpyAsync(x.d, x.h, x.n, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
+    }
+    rc = hmm_loglik_batched(c, n_prop, K, dpi, dP, dp, dmu, dcov, n_seg, offs,
+                            T_total ? dxy : nullptr, T_total ? dtr : nullptr, opts, dout, stream);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(out_host, dout, 8 * (size_t)n_prop, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
+    return hmm_status(c, stream);
+}
+
+}  // extern "C"
