@@ -10,6 +10,7 @@
 // Every launch goes to the caller's stream; nothing synchronises unless the
 // caller asks (hmm_status, or the _host entry point).
 #include <algorithm>
+#include <climits>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -61,6 +62,7 @@ struct hmm_ctx {
     Plan plan;
     int last_launches = 0;
     int last_L = 0;
+    int n_sms = 0;
     // phase timing
     bool prof_on = false;
     bool prof_pending = false;
@@ -134,10 +136,31 @@ struct Carve {
     }
 };
 
-static int choose_chunk_len(int precision, int n_prop, int KP, int64_t steps_total) {
+static int choose_chunk_len(int precision, int n_prop, int KP, int64_t steps_total, int n_sms) {
+    if (precision != HMM_PREC_FP32_SIMT) {
+        // persistent tensor-core kernel: one work item = chunks_per_item chunks of
+        // one proposal on one SM; minimise (waves x chunk length), i.e. the
+        // critical path, preferring longer chunks (a smaller tree) on ties
+        const int per_item = chunk_tc_chunks_per_item(KP);
+        int64_t best_cost = INT64_MAX;
+        int best_L = OBS_WIN;
+        for (int L = OBS_WIN; L <= 16384; L += OBS_WIN) {
+            int64_t C = (steps_total + L - 1) / L;
+            if (C < 1) C = 1;
+            int64_t items = (int64_t)n_prop * ((C + per_item - 1) / per_item);
+            int64_t waves = (items + n_sms - 1) / n_sms;
+            int64_t cost = waves * L;
+            if (cost <= best_cost) {
+                best_cost = cost;
+                best_L = L;
+            }
+            if (C == 1) break;
+        }
+        return best_L;
+    }
     // enough independent rows to fill the GPU a few times over, chunk length
     // a multiple of the 64-step observation window
-    double rows_target = precision == HMM_PREC_FP32_SIMT ? 152.0 * 2048.0 : 152.0 * 1024.0;
+    double rows_target = (double)n_sms * 2048.0;
     double chunks_target = rows_target / ((double)n_prop * KP);
     if (chunks_target < 1.0) chunks_target = 1.0;
     double L = (double)steps_total / chunks_target;
@@ -396,7 +419,8 @@ int hmm_loglik_batched(hmm_ctx *c, int32_t n_prop, int32_t K, const float *pi, c
     ConstLayout lay = make_layout(K, prec);
     int64_t steps_total = 0;
     for (int s = 0; s < n_seg; ++s) steps_total += std::max<int64_t>(0, offs[s + 1] - offs[s] - 1);
-    int L = opts.chunk_len ? opts.chunk_len : choose_chunk_len(prec, n_prop, lay.KP, steps_total);
+    if (!c->n_sms) cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, c->device);
+    int L = opts.chunk_len ? opts.chunk_len : choose_chunk_len(prec, n_prop, lay.KP, steps_total, c->n_sms);
     if (!plan_matches(c->plan, K, n_prop, n_seg, offs, prec, L)) {
         build_plan(c->plan, K, n_prop, n_seg, offs, prec, L);
         if (c->plan.n_levels + 1 > MAX_LEVELS) {

@@ -146,6 +146,10 @@ chunk_simt_kernel(int n_chunks, int L, int renorm, ConstLayout lay, const float 
     }
     if (bad) atomicOr(status, ST_ENUMERIC);
     if (live) {
+        float mx = 0.0f;
+#pragma unroll
+        for (int j = 0; j < KP; ++j) mx = fmaxf(mx, row[j]);
+        if (!(mx > 0.0f)) expo = ZERO_ROW_EXP32;
         float *dst = A0 + ((size_t)q * n_chunks + j_chunk) * KP * KP + (size_t)i * KP;
 #pragma unroll
         for (int j4 = 0; j4 < KP / 4; ++j4)

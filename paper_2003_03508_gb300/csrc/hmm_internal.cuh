@@ -42,7 +42,12 @@ enum {
 };
 
 // a step whose best state has log2-emission below -EXP_LIMIT is not representable
-constexpr int EXP_LIMIT = 1 << 17;
+// (keeps a chunk's exponent sum, <= 16384 steps, inside int32)
+constexpr int EXP_LIMIT = 1 << 16;
+// exponent recorded for an all-zero row (its scale is irrelevant); the tree
+// aligns rows to the largest exponent, so zero rows must never win that max
+constexpr int32_t ZERO_ROW_EXP32 = INT32_MIN;
+constexpr long long ZERO_ROW_EXP64 = -(1LL << 62);
 constexpr int MAX_LEVELS = 10;
 constexpr int TREE_GROUP = 16;
 constexpr int OBS_WIN = 64;   // steps per observation window; chunk lengths are multiples
@@ -129,6 +134,7 @@ cudaError_t launch_chunk_simt(int n_prop, int n_chunks, int L, int renorm, const
                               float *A0, int32_t *e0, unsigned *status, cudaStream_t st);
 
 bool chunk_tc_supported(int K, int precision);
+int chunk_tc_chunks_per_item(int KP);
 cudaError_t launch_chunk_tc(int n_prop, int n_chunks, int L, int renorm, int precision,
                             const ConstLayout &lay, const float *cblock, const ChunkDesc *chunks,
                             const float2 *packed, float *A0, int32_t *e0, unsigned *status,

@@ -46,7 +46,10 @@ tree_level_kernel(int KP, int level, const TreeGroup *__restrict__ groups, Level
     const int lane = tid & 31, warp = tid >> 5, nwarps = TREE_THREADS / 32;
 
     auto load_e = [&](size_t m, int k) -> long long {
-        if (E32) return (long long)reinterpret_cast<const int32_t *>(lv.e[level])[((size_t)q * nin + m) * KP + k];
+        if (E32) {
+            int32_t v = reinterpret_cast<const int32_t *>(lv.e[level])[((size_t)q * nin + m) * KP + k];
+            return v == ZERO_ROW_EXP32 ? ZERO_ROW_EXP64 : (long long)v;
+        }
         return reinterpret_cast<const long long *>(lv.e[level])[((size_t)q * nin + m) * KP + k];
     };
 
@@ -91,15 +94,16 @@ tree_level_kernel(int KP, int level, const TreeGroup *__restrict__ groups, Level
             float mx = 0.0f;
             for (int j = lane; j < KP; j += 32) mx = fmaxf(mx, X[i * KP + j]);
             for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            int r = 0;
             if (mx > 0.0f) {
                 if (!isfinite(mx)) bad = true;
-                r = float_exponent(mx);
+                int r = float_exponent(mx);
                 r = r < -126 ? -126 : (r > 126 ? 126 : r);
                 float s = pow2f(-r);
                 for (int j = lane; j < KP; j += 32) X[i * KP + j] *= s;
+                if (lane == 0) ex[i] += M + r;
+            } else if (lane == 0) {
+                ex[i] = ZERO_ROW_EXP64;
             }
-            if (lane == 0) ex[i] += M + r;
         }
         __syncthreads();
     }
@@ -208,9 +212,10 @@ final_kernel(int K, int KP, int init_mode, int n_seg, const SegFinal *__restrict
                 double lh = lpi0[k] + le;
                 if (sf.level >= 0) {
                     long long e;
-                    if (sf.level == 0)
-                        e = reinterpret_cast<const int32_t *>(lv.e[0])[((size_t)q * lv.n[0] + sf.idx) * KP + k];
-                    else
+                    if (sf.level == 0) {
+                        int32_t e32 = reinterpret_cast<const int32_t *>(lv.e[0])[((size_t)q * lv.n[0] + sf.idx) * KP + k];
+                        e = e32 == ZERO_ROW_EXP32 ? ZERO_ROW_EXP64 : (long long)e32;
+                    } else
                         e = reinterpret_cast<const long long *>(lv.e[sf.level])[((size_t)q * lv.n[sf.level] + sf.idx) * KP + k];
                     lh += (double)e * LN2;
                 }

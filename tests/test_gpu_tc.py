@@ -1,0 +1,120 @@
+"""Parity of the tensor-core (tcgen05) chunk products with the FP64 oracle.
+
+Tolerance for TF32 / BF16 / TF32-split chunk products: |d| <= 1e-4 |log L|
+(relative in log L), with an absolute floor of 1e-3 for tiny sequences. The
+error budget behind it: the running product is rounded to the operand type
+every step (unbiased, O(sqrt(T) u) in log L with u = 2^-11 for TF32, 2^-9
+for BF16), and P is rounded once (a bias of at most ~T u / sqrt(K) in log L;
+removed to O(u^2) by the hi+lo split used for BF16 and TF32-split). Each
+test also reports the observed error so the per-dtype figures can be read
+off the log.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2003_03508_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TC_REL, TC_ABS = 1e-4, 1e-3
+PRECS = ["tf32", "tf32_split", "bf16"]
+
+
+def _run(api, prm, xy, tremor, **opt):
+    ctx = api.default_context()
+    out = ctx.hmm_loglik(*api.to_device(prm), torch.from_numpy(np.ascontiguousarray(xy)).cuda(),
+                         torch.from_numpy(np.ascontiguousarray(tremor)).cuda(), opts=api.make_opts(**opt))
+    torch.cuda.synchronize()
+    return float(out.item())
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("K", [1, 4, 16, 17, 25, 32])
+def test_tc_parity_sizes(cuda_lib, K, prec):
+    rng = np.random.default_rng(2000 + K)
+    prm = synth.random_params(K, rng)
+    T = 5000 + 37
+    obs = synth.sample_observations(prm, T, rng)
+    ref = oracle.loglik(prm, obs.xy, obs.tremor)
+    for L in (64, 256, 0):
+        got = _run(cuda_lib, prm, obs.xy, obs.tremor, precision=prec, chunk_len=L)
+        err = abs(got - ref)
+        print(f"K={K} {prec} L={L}: rel err {err / abs(ref):.2e}")
+        assert err <= TC_REL * abs(ref) + TC_ABS, (K, prec, L, got, ref)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("T", [0, 1, 2, 65, 130])
+def test_tc_small_T(cuda_lib, prec, T):
+    rng = np.random.default_rng(300 + T)
+    prm = synth.random_params(9, rng)
+    obs = synth.sample_observations(prm, T, rng)
+    ref = oracle.loglik(prm, obs.xy, obs.tremor)
+    got = _run(cuda_lib, prm, obs.xy, obs.tremor, precision=prec, chunk_len=64)
+    assert abs(got - ref) <= TC_REL * abs(ref) + TC_ABS, (T, got, ref)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_tc_batched_segments(cuda_lib, prec):
+    api = cuda_lib
+    d = synth.batched_inputs(K=32, T=80_000, n_prop=12, seed=5, n_seg=7)
+    ctx = api.default_context()
+    got = ctx.hmm_loglik_batched(*api.to_device(d["params"]), d["offsets"],
+                                 torch.from_numpy(d["xy"]).cuda(), torch.from_numpy(d["tremor"]).cuda(),
+                                 opts=api.make_opts(precision=prec, chunk_len=256)).cpu().numpy()
+    ref = oracle.loglik_batched(d["params"], d["xy"], d["tremor"], d["offsets"], n_threads=4)
+    rel = np.abs(got - ref) / np.abs(ref)
+    print(f"{prec} batched max rel err {rel.max():.2e}")
+    assert np.all(rel <= TC_REL), rel
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_tc_bit_reproducible(cuda_lib, prec):
+    d = synth.config_inputs("k4_t1e4")
+    a = _run(cuda_lib, d["params"], d["xy"], d["tremor"], precision=prec)
+    b = _run(cuda_lib, d["params"], d["xy"], d["tremor"], precision=prec)
+    assert a == b
+
+
+def test_tc_zero_likelihood(cuda_lib):
+    rng = np.random.default_rng(3)
+    prm = synth.random_params(8, rng)
+    prm.p_tremor[:] = 0.0
+    xy = np.zeros((700, 2), np.float32)
+    fl = np.zeros(700, np.uint8)
+    fl[400] = 1
+    assert _run(cuda_lib, prm, xy, fl, precision="tf32", chunk_len=64) == -math.inf
+
+
+def test_tc_k25_t2p20(cuda_lib):
+    d = synth.config_inputs("k25_t2p20")
+    ref = oracle.loglik(d["params"], d["xy"], d["tremor"])
+    for prec in PRECS:
+        got = _run(cuda_lib, d["params"], d["xy"], d["tremor"], precision=prec)
+        print(f"K=25 T=2^20 {prec}: rel err {abs(got - ref) / abs(ref):.2e}, abs {abs(got - ref):.3f}")
+        assert abs(got - ref) <= TC_REL * abs(ref)
+
+
+def test_bench_workload_sampled(cuda_lib):
+    """K=32, T=2^20, 256 proposals, automatic chunking (the benchmark's launch):
+    TF32 against the oracle on sampled proposals, and against FP32-SIMT on all."""
+    api = cuda_lib
+    d = synth.batched_inputs(K=32, T=1 << 20, n_prop=256, seed=3)
+    ctx = api.default_context()
+    dev = api.to_device(d["params"])
+    xy = torch.from_numpy(d["xy"]).cuda()
+    fl = torch.from_numpy(d["tremor"]).cuda()
+    tc = ctx.hmm_loglik_batched(*dev, d["offsets"], xy, fl, opts=api.make_opts(precision="tf32")).cpu().numpy()
+    fp = ctx.hmm_loglik_batched(*dev, d["offsets"], xy, fl, opts=api.make_opts(precision="fp32")).cpu().numpy()
+    assert ctx.hmm_status() == api.HMM_OK
+    assert np.all(np.abs(tc - fp) <= TC_REL * np.abs(fp))
+    pick = [0, 77, 200, 255]
+    sub = type(d["params"])(*(a[pick] for a in d["params"].as_tuple()))
+    ref = oracle.loglik_batched(sub, d["xy"], d["tremor"], d["offsets"], n_threads=4)
+    print("sampled rel err tf32", np.abs(tc[pick] - ref) / np.abs(ref), "fp32", np.abs(fp[pick] - ref) / np.abs(ref))
+    assert np.all(np.abs(tc[pick] - ref) <= TC_REL * np.abs(ref))
+    assert np.all(np.abs(fp[pick] - ref) <= 1e-6 * np.abs(ref))
