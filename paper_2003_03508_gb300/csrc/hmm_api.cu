@@ -139,9 +139,11 @@ struct Carve {
 static int choose_chunk_len(int precision, int n_prop, int KP, int64_t steps_total, int n_sms) {
     if (precision != HMM_PREC_FP32_SIMT) {
         // persistent tensor-core kernel: one work item = chunks_per_item chunks of
-        // one proposal on one SM; minimise (waves x chunk length), i.e. the
-        // critical path, preferring longer chunks (a smaller tree) on ties
-        const int per_item = chunk_tc_chunks_per_item(KP);
+        // one proposal on one SM; minimise the critical path, waves x (chunk
+        // length + per-item start-up, about 64 steps), plus the product tree
+        // (one K^3 product per chunk, about 1/16 of a chunk step per chunk on
+        // the whole GPU), preferring longer chunks on ties
+        const int per_item = chunk_tc_chunks_per_item(KP, precision);
         int64_t best_cost = INT64_MAX;
         int best_L = OBS_WIN;
         for (int L = OBS_WIN; L <= 16384; L += OBS_WIN) {
@@ -149,7 +151,7 @@ static int choose_chunk_len(int precision, int n_prop, int KP, int64_t steps_tot
             if (C < 1) C = 1;
             int64_t items = (int64_t)n_prop * ((C + per_item - 1) / per_item);
             int64_t waves = (items + n_sms - 1) / n_sms;
-            int64_t cost = waves * L;
+            int64_t cost = waves * (L + 64) + (int64_t)n_prop * C / (16 * n_sms);
             if (cost <= best_cost) {
                 best_cost = cost;
                 best_L = L;

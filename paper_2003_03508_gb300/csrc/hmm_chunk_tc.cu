@@ -12,15 +12,18 @@
 // B operand P:
 //     D[r][n] = sum_k A[r][k] P[k][n]            (tcgen05.mma, FP32 in TMEM)
 //     A'[r][n] = D[r][n] * D_t(chunk(r))[n]      (epilogue, registers)
-// A lives in shared memory (K-major, canonical no-swizzle layout), P arrives
-// by a TMA bulk copy, D is an FP32 accumulator in tensor memory. A CTA keeps
-// G such 128-row groups in flight so the tensor core works on one group while
-// the epilogue warps scale and write back the others.
+// Both A and the FP32 accumulator D live in tensor memory (TMEM): with N = KP
+// as small as 32, an A operand in shared memory would be re-read by every MMA
+// and rewritten by every epilogue, and shared-memory bandwidth, not the tensor
+// core, would set the pace. P (the B operand, canonical K-major no-swizzle
+// layout) arrives in shared memory by a TMA bulk copy. A CTA keeps G such
+// 128-row groups in flight so the tensor core works on one group while the
+// epilogue warps scale and write back the others.
 //
-// Warp roles: warp 0 allocates TMEM and one lane issues every MMA; warps
-// 4..4+4E-1 are the epilogue (warp w reads TMEM lanes 32*(w%4)..+31 and owns
-// those rows of groups g = team, team+E, ...). Warps 1-3 only join the final
-// barrier.
+// Warp roles: warp 0 allocates TMEM; lane 0 of warps 0..3 issue the MMAs
+// (issuer w serves groups g = w mod 4); warps 4..4+4E-1 are the epilogue
+// (warp w reads TMEM lanes 32*(w%4)..+31 and owns those rows of groups
+// g = team, team+E, ...).
 //
 // Every wait is bounded: a wait that runs out sets the context's ETIMEOUT
 // status bit and an abort flag; all warps then drain (in-flight copies and
@@ -34,6 +37,7 @@ namespace hmm {
 namespace {
 
 constexpr int TC_M = 128;
+constexpr int NISS = 4;  // MMA issuer warps (warps 0..3)
 constexpr long long SPIN_LIMIT_CYCLES = 4000000000LL;  // about 2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -59,6 +63,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// non-blocking probe of one phase (never suspends the thread)
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(smem_u32(bar)), "r"(parity)
@@ -117,20 +134,21 @@ __host__ __device__ constexpr uint32_t instr_desc(int n) {
            ((uint32_t)(TC_M >> 4) << 24);
 }
 
+// D (TMEM) = A (TMEM) x B (shared memory), or D += A x B
 template <int PREC>
-__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                    uint32_t accumulate) {
+__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
     if constexpr (PREC == HMM_PREC_BF16) {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
             : "memory");
     } else {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
             : "memory");
     }
 }
@@ -159,9 +177,60 @@ __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 16 registers per thread into 32 lanes x 16 columns of TMEM
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t *r) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+
+// one thread's row of NC consecutive 32-bit TMEM columns (NC = 8, 16 or 32)
+template <int NC>
+__device__ __forceinline__ void tmem_st_row(uint32_t taddr, const uint32_t *r) {
+    static_assert(NC == 8 || NC % 16 == 0, "row width");
+    if constexpr (NC == 8) {
+        tmem_st8(taddr, r);
+    } else {
+#pragma unroll
+        for (int c = 0; c < NC / 16; ++c) tmem_st16(taddr + c * 16, r + c * 16);
+    }
+}
+
+__device__ __forceinline__ void tmem_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// FP32 -> TF32 operand, round to nearest with ties away from zero: add half a
+// TF32 unit in the last place to the bit pattern (integer pipe; overflow
+// rounds to infinity as it should). The tensor core reads a TF32 operand from
+// the top 19 bits and ignores the 13 low bits, so they need not be cleared;
+// the parity tests pin this (identical results with and without the mask).
 __device__ __forceinline__ uint32_t to_tf32_bits(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __float_as_uint(x) + 0x1000u;
+}
+
+// nearest integer to m (|m| < 2^22) and the same value as a float, without
+// the conversion pipe: add and subtract 1.5 * 2^23
+__device__ __forceinline__ int round_to_int(float m, float &mf) {
+    const float magic = 12582912.0f;
+    const float t = __fadd_rn(m, magic);
+    mf = __fsub_rn(t, magic);
+    return __float_as_int(t) - 0x4B400000;
+}
+
+// 2^x on the special-function unit (FTZ: results below 2^-126 flush to 0)
+__device__ __forceinline__ float ex2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
 
@@ -186,6 +255,48 @@ __device__ __forceinline__ bool named_barrier_or(int id, int nthreads, bool pred
     return r != 0;
 }
 
+// packed FP32 pair helpers (sm_100+ f32x2 arithmetic)
+__device__ __forceinline__ unsigned long long pack2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void unpack2(unsigned long long v, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// maximum over the KP lanes of each chunk (KP = 32: whole warp, KP = 16: halves)
+template <int KP>
+__device__ __forceinline__ float chunk_max(float v, int lane) {
+    if constexpr (KP == 32) {
+        float m;
+        asm("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(m) : "f"(v));
+        return m;
+    } else {
+        float lo = lane < 16 ? v : -INFINITY, hi = lane < 16 ? -INFINITY : v, m0, m1;
+        asm("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(m0) : "f"(lo));
+        asm("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(m1) : "f"(hi));
+        return lane < 16 ? m0 : m1;
+    }
+}
+
 template <int KP, int PREC, int G, int E>
 struct TcCfg {
     static constexpr int ESZ = PREC == HMM_PREC_BF16 ? 2 : 4;  // bytes per operand element
@@ -195,35 +306,40 @@ struct TcCfg {
     static constexpr int CPW = 32 / KP;                         // chunks per warp
     static constexpr int CPG = TC_M / KP;                       // chunks per group
     static constexpr int GPW = G / E;                           // groups per epilogue warp
-    static constexpr int SBO = KP * ESZ * 8;                    // bytes between 8-row groups
-    static constexpr int A_BYTES = TC_M * KP * ESZ;             // one group's A operand
+    static constexpr int SBO = KP * ESZ * 8;                    // bytes between 8-row groups of P
+    static constexpr int KA = KP * ESZ / 4;                     // TMEM columns of one A row
     static constexpr int P_BYTES = KP * KP * ESZ * NIMG;
-    static constexpr int NWIN = OBS_WIN / KP;                   // window entries per lane
+    static constexpr int WIN = KP == 32 ? 64 : 32;              // observation window (steps)
+    static constexpr int NWIN = WIN / KP;                       // window entries per lane
     static constexpr int EPI_WARPS = 4 * E;
     static constexpr int THREADS = 32 * (4 + EPI_WARPS);
-    static constexpr int TMEM_COLS = (G * KP <= 32) ? 32 : (G * KP <= 64) ? 64 : (G * KP <= 128) ? 128
-                                     : (G * KP <= 256) ? 256 : 512;
+    // TMEM: G accumulators D (KP columns each), then G running products A (KA columns each)
+    static constexpr int TMEM_USED = G * (KP + KA);
+    static constexpr int TMEM_COLS = (TMEM_USED <= 32) ? 32 : (TMEM_USED <= 64) ? 64 : (TMEM_USED <= 128) ? 128
+                                     : (TMEM_USED <= 256) ? 256 : 512;
+    static constexpr int A_COL0 = G * KP;
     // shared memory carve (bytes)
-    static constexpr int OFF_A = 0;
-    static constexpr int OFF_P = OFF_A + G * A_BYTES;
+    static constexpr int OFF_P = 0;
     static constexpr int OFF_OBS = OFF_P + ((P_BYTES + 127) / 128) * 128;
-    static constexpr int OBS_BYTES = EPI_WARPS * GPW * CPW * OBS_WIN * 8;
+    static constexpr int OBS_BYTES = EPI_WARPS * GPW * CPW * 2 * WIN * 8;  // double buffered
     static constexpr int OFF_D = OFF_OBS + OBS_BYTES;
-    static constexpr int OFF_BAR = OFF_D + EPI_WARPS * 32 * 4;
-    static constexpr int NBAR = 2 * G + 2;  // full[G], empty[G], pload, drain
+    static constexpr int D_BYTES = EPI_WARPS * GPW * 32 * 4;
+    static constexpr int OFF_BAR = OFF_D + D_BYTES;
+    static constexpr int NBAR = 2 * G + 1 + 4;  // full[G], empty[G], pload, drain[4]
     static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
     static constexpr int SMEM = OFF_MISC + 16 + 1024;  // + slack for 1 KB alignment
     static_assert(G % E == 0, "groups must split evenly over epilogue teams");
     static_assert(KP == 16 || KP == 32, "this tile shape covers KP = 16 and 32");
-    static_assert(G * KP <= 512, "TMEM holds 512 FP32 columns");
+    static_assert(TMEM_USED <= 512, "TMEM holds 512 32-bit columns");
+    static_assert(G <= 32, "group bitmasks are 32-bit");
+    static_assert(SMEM <= 232448, "shared memory per CTA");
 };
 
 template <int KP, int PREC, int G, int E>
 __global__ void __launch_bounds__(TcCfg<KP, PREC, G, E>::THREADS, 1)
-chunk_tc_kernel(int n_prop, int n_chunks, int renorm, int K, ConstLayout lay,
-                const float *__restrict__ cblock, const ChunkDesc *__restrict__ chunks,
-                const float2 *__restrict__ packed, float *__restrict__ A0, int32_t *__restrict__ e0,
-                unsigned *__restrict__ status) {
+chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const float *__restrict__ cblock,
+                const ChunkDesc *__restrict__ chunks, const float2 *__restrict__ packed,
+                float *__restrict__ A0, int32_t *__restrict__ e0, unsigned *__restrict__ status) {
     using C = TcCfg<KP, PREC, G, E>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -231,7 +347,7 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, int K, ConstLayout lay,
     uint64_t *full = bars;
     uint64_t *empty = bars + G;
     uint64_t *pload = bars + 2 * G;
-    uint64_t *drain = bars + 2 * G + 1;
+    uint64_t *drain = bars + 2 * G + 1;  // one per issuer
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + C::OFF_MISC);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + C::OFF_MISC + 4);
 
@@ -247,7 +363,7 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, int K, ConstLayout lay,
             mbar_init(&empty[g], 4);  // one arrival per lane-quadrant warp of the team
         }
         mbar_init(pload, 1);
-        mbar_init(drain, 1);
+        for (int w = 0; w < NISS; ++w) mbar_init(&drain[w], 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -269,15 +385,17 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, int K, ConstLayout lay,
         return s;
     };
 
-    if (warp == 0) {
-        // ---------------- MMA issuer ----------------
+    if (warp < NISS) {
+        // ---------------- MMA issuers ----------------
+        // One thread issues a tcgen05.mma only every few tens of cycles, far less
+        // work than one M=128, N=KP MMA holds, so four warps (one per SM
+        // sub-partition) issue in parallel; issuer w owns groups g = w (mod 4)
+        // and serves them in order.
         if (lane == 0) {
             const uint32_t idesc = instr_desc<PREC>(KP);
-            const uint32_t a_base = smem_u32(smem + C::OFF_A);
             const uint32_t p_base = smem_u32(smem + C::OFF_P);
             uint32_t empty_par = 0, pload_par = 0;
-            bool ok = true;
-            bool issued = false;
+            bool ok = true, issued = false;
             for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
                 const int b = item % items_per_prop;
                 const int steps = item_steps(b);
@@ -285,20 +403,20 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, int K, ConstLayout lay,
                 ok = mbar_wait(pload, pload_par, abort_flag, status);
                 pload_par ^= 1;
                 for (int t = 0; t < steps && ok; ++t) {
-                    for (int g = 0; g < live_groups && ok; ++g) {
+                    for (int g = warp; g < live_groups && ok; g += NISS) {
                         ok = mbar_wait(&empty[g], (empty_par >> g) & 1u, abort_flag, status);
                         if (!ok) break;
                         empty_par ^= 1u << g;
                         tc_fence_after();
                         const uint32_t d_tmem = tmem_base + (uint32_t)(g * KP);
-                        const uint32_t a_g = a_base + (uint32_t)(g * C::A_BYTES);
+                        const uint32_t a_tmem = tmem_base + (uint32_t)(C::A_COL0 + g * C::KA);
 #pragma unroll
                         for (int img = 0; img < C::NIMG; ++img) {
 #pragma unroll
                             for (int ks = 0; ks < C::NKS; ++ks) {
-                                const uint64_t ad = smem_desc(a_g + ks * 256, 128, C::SBO);
+                                // one MMA consumes 32 bytes of K: 8 TMEM columns of A
                                 const uint64_t bd = smem_desc(p_base + img * (KP * KP * C::ESZ) + ks * 256, 128, C::SBO);
-                                mma<PREC>(d_tmem, ad, bd, idesc, (img | ks) != 0);
+                                mma_ts<PREC>(d_tmem, a_tmem + ks * 8, bd, idesc, (img | ks) != 0);
                             }
                         }
                         mma_commit(&full[g]);
@@ -307,10 +425,10 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, int K, ConstLayout lay,
                 }
             }
             if (issued) {
-                // every MMA issued so far completes before the TMEM is freed
-                mma_commit(drain);
+                // every MMA this thread issued completes before the TMEM is freed
+                mma_commit(&drain[warp]);
                 const long long t0 = clock64();
-                while (!mbar_try_wait(drain, 0) && clock64() - t0 < SPIN_LIMIT_CYCLES) {
+                while (!mbar_try_wait(&drain[warp], 0) && clock64() - t0 < SPIN_LIMIT_CYCLES) {
                 }
             }
         }
@@ -325,13 +443,18 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, int K, ConstLayout lay,
         const int i = r % KP;             // start state / state index of this lane
         const int half = lane / KP;       // chunk within the warp
         const int jl = lane % KP;         // lane within its chunk
-        float2 *sObs = reinterpret_cast<float2 *>(smem + C::OFF_OBS) + (size_t)ew * C::GPW * C::CPW * OBS_WIN;
-        float *sD = reinterpret_cast<float *>(smem + C::OFF_D) + ew * 32;
-        const uint32_t a_base = smem_u32(smem + C::OFF_A);
+        float2 *sObs = reinterpret_cast<float2 *>(smem + C::OFF_OBS) + (size_t)ew * C::GPW * C::CPW * 2 * C::WIN;
+        float *sD = reinterpret_cast<float *>(smem + C::OFF_D) + ew * C::GPW * 32;
+        const uint32_t tm_row = tmem_base + ((uint32_t)(quad * 32) << 16);
         const int nthr_epi = 32 * C::EPI_WARPS;
         uint32_t full_par = 0, pload_issued = 0;
         int cur_q = -1;
         float mux = 0.f, muy = 0.f, qa = 0.f, qb = 0.f, qc = 0.f, ctr = -INFINITY, cno = -INFINITY;
+
+        // window buffer for (group slot u, buffer b) of this lane's chunk
+        auto win_ptr = [&](int u, int bsel) {
+            return sObs + (((size_t)u * C::CPW + half) * 2 + bsel) * C::WIN;
+        };
 
         for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
             // previous item fully consumed by every epilogue warp (so every MMA
@@ -361,75 +484,74 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, int K, ConstLayout lay,
                 cno = em[EM_CNO * KP + i];
                 cur_q = q;
             }
-            // per group state of this lane's chunk
             int64_t pstart[C::GPW];
             int len[C::GPW];
-            int jchunk[C::GPW];
             int expo[C::GPW];
-            bool glive[C::GPW];
-            float2 pf[C::GPW][C::NWIN];
+            uint32_t glive = 0;
 #pragma unroll
             for (int u = 0; u < C::GPW; ++u) {
                 const int g = team + E * u;
                 const int jg = b * per_item + g * C::CPG;
-                glive[u] = jg < n_chunks;
+                if (jg < n_chunks) glive |= 1u << u;
                 const int j = jg + cs;
-                jchunk[u] = j;
                 expo[u] = 0;
-                if (j < n_chunks) {
-                    pstart[u] = chunks[j].pstart;
-                    len[u] = chunks[j].len;
-                } else {
-                    pstart[u] = 0;
-                    len[u] = 0;
-                }
-                if (!glive[u]) continue;
-                // running product starts as the identity row e_i
-                const uint32_t arow = a_base + g * C::A_BYTES + (r >> 3) * C::SBO + (r & 7) * 16;
+                pstart[u] = j < n_chunks ? chunks[j].pstart : 0;
+                len[u] = j < n_chunks ? chunks[j].len : 0;
+                if (!(glive >> u & 1u)) continue;
+                // running product starts as the identity row e_i (in TMEM)
+                {
+                    uint32_t w[C::KA];
 #pragma unroll
-                for (int kc = 0; kc < KP * C::ESZ / 16; ++kc) {
-                    uint32_t w[4] = {0u, 0u, 0u, 0u};
-                    if constexpr (C::ESZ == 4) {
-                        if (i / 4 == kc) w[i % 4] = 0x3f800000u;  // 1.0f
-                    } else {
-                        if (i / 8 == kc) w[(i % 8) / 2] = (i % 2) ? 0x3f800000u : 0x00003f80u;  // bf16 1.0
+                    for (int c = 0; c < C::KA; ++c) {
+                        if constexpr (C::ESZ == 4) w[c] = (c == i) ? 0x3f800000u : 0u;  // 1.0f
+                        else w[c] = (c == i / 2) ? ((i & 1) ? 0x3f800000u : 0x00003f80u) : 0u;  // bf16 1.0
                     }
-                    st_shared_v4(arow + kc * 128, w[0], w[1], w[2], w[3]);
+                    tmem_st_row<C::KA>(tm_row + C::A_COL0 + g * C::KA, w);
+                    tmem_wait_st();
                 }
-                fence_proxy_async_smem();
+                tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[g]);
-                // prefetch the first observation window of this lane's chunk
+            }
+            // observation windows 0 and 1 of every chunk (asynchronous copies)
 #pragma unroll
-                for (int v = 0; v < C::NWIN; ++v) {
-                    const int s = jl + KP * v;
-                    pf[u][v] = (s < len[u]) ? packed[pstart[u] + s]
-                                            : make_float2(__int_as_float(0x7fc00000), 0.f);
+            for (int wdw = 0; wdw < 2; ++wdw) {
+#pragma unroll
+                for (int u = 0; u < C::GPW; ++u) {
+#pragma unroll
+                    for (int v = 0; v < C::NWIN; ++v) {
+                        const int s = wdw * C::WIN + jl + KP * v;
+                        if (s < len[u]) cp_async8(smem_u32(win_ptr(u, wdw) + jl + KP * v), packed + pstart[u] + s);
+                    }
                 }
+                cp_async_commit();
             }
 
             for (int t = 0; t < steps; ++t) {
-                const int w = t % OBS_WIN;
+                const int w = t % C::WIN;
+                const int bsel = (t / C::WIN) & 1;
+                if (w == 0) {
+                    if (t > 0) {
+                        // refill the buffer that window t/WIN - 1 used with window t/WIN + 1
+#pragma unroll
+                        for (int u = 0; u < C::GPW; ++u) {
+#pragma unroll
+                            for (int v = 0; v < C::NWIN; ++v) {
+                                const int s = t + C::WIN + jl + KP * v;
+                                if (s < len[u]) cp_async8(smem_u32(win_ptr(u, bsel ^ 1) + jl + KP * v), packed + pstart[u] + s);
+                            }
+                        }
+                        cp_async_commit();
+                    }
+                    cp_async_wait1();
+                    __syncwarp();
+                }
+                // Step 1 fused: emissions of every group's chunk at step t (log2),
+                // prescale exponent, D_t into shared memory
+                int Et[C::GPW];
 #pragma unroll
                 for (int u = 0; u < C::GPW; ++u) {
-                    if (!glive[u]) continue;
-                    const int g = team + E * u;
-                    float2 *win = sObs + ((size_t)u * C::CPW + half) * OBS_WIN;
-                    if (w == 0) {
-                        __syncwarp();
-#pragma unroll
-                        for (int v = 0; v < C::NWIN; ++v) win[jl + KP * v] = pf[u][v];
-                        __syncwarp();
-#pragma unroll
-                        for (int v = 0; v < C::NWIN; ++v) {
-                            const int s = t + OBS_WIN + jl + KP * v;
-                            pf[u][v] = (s < len[u]) ? packed[pstart[u] + s]
-                                                    : make_float2(__int_as_float(0x7fc00000), 0.f);
-                        }
-                    }
-                    const bool act = t < len[u];
-                    // Step 1 fused: emission of state i for this chunk's step t (log2)
-                    const float2 o = win[w];
+                    const float2 o = win_ptr(u, bsel)[w];
                     float l;
                     if (isnan(o.x)) {
                         l = cno;
@@ -437,97 +559,104 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, int K, ConstLayout lay,
                         const float dx = o.x - mux, dy = o.y - muy;
                         l = fmaf(qa * dx, dx, fmaf(qb * dx, dy, fmaf(qc * dy, dy, ctr)));
                     }
-                    float m = l;
-#pragma unroll
-                    for (int off = KP / 2; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-                    int Et = 0;
+                    const float m = chunk_max<KP>(l, lane);
                     float d;
+                    Et[u] = 0;
                     if (m >= -(float)EXP_LIMIT) {
-                        Et = (int)floorf(m);
-                        d = exp2f(l - (float)Et);
+                        // prescale by the nearest power of two: the best state's
+                        // factor lies in [2^-0.5, 2^0.5]
+                        float mf;
+                        Et[u] = round_to_int(m, mf);
+                        d = ex2_approx(l - mf);
                     } else {
-                        if (m != -INFINITY && act) atomicOr(status, ST_ENUMERIC);
+                        if (m != -INFINITY && t < len[u]) atomicOr(status, ST_ENUMERIC);
                         d = 0.0f;
                     }
-                    sD[lane] = d;
-                    __syncwarp();
-                    // the MMA for this step has finished (warp-uniform decision)
-                    const bool ok = __all_sync(0xffffffffu, mbar_wait(&full[g], (full_par >> g) & 1u, abort_flag, status));
+                    sD[u * 32 + lane] = d;
+                }
+                __syncwarp();
+                // products of this step, group by group
+#pragma unroll
+                for (int u = 0; u < C::GPW; ++u) {
+                    const int g = team + E * u;
+                    if (!(glive >> u & 1u)) continue;
+                    const bool okw = __all_sync(0xffffffffu, mbar_wait(&full[g], (full_par >> g) & 1u, abort_flag, status));
                     full_par ^= 1u << g;
-                    if (ok) {
+                    float a[KP];
+                    if (okw) {
                         tc_fence_after();
-                        float acc[KP];
-                        const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(g * KP);
 #pragma unroll
-                        for (int c16 = 0; c16 < KP / 16; ++c16) tmem_ld16(taddr + c16 * 16, acc + c16 * 16);
+                        for (int c16 = 0; c16 < KP / 16; ++c16) tmem_ld16(tm_row + g * KP + c16 * 16, a + c16 * 16);
                         tmem_wait_ld();
-                        if (act) {
-                            // Step 2 fused: column scale by D_t
-                            const float4 *dv = reinterpret_cast<const float4 *>(sD + half * KP);
+                    }
+                    if (okw && t < len[u]) {
+                        // Step 2 fused: column scale by D_t (pairs)
+                        const float4 *dv = reinterpret_cast<const float4 *>(sD + u * 32 + half * KP);
 #pragma unroll
-                            for (int j4 = 0; j4 < KP / 4; ++j4) {
-                                const float4 dd = dv[j4];
-                                acc[4 * j4 + 0] *= dd.x;
-                                acc[4 * j4 + 1] *= dd.y;
-                                acc[4 * j4 + 2] *= dd.z;
-                                acc[4 * j4 + 3] *= dd.w;
-                            }
-                            expo[u] += Et;
-                            const bool last = (t + 1 == len[u]);
-                            if ((t + 1) % renorm == 0 || last) {
-                                float mx = 0.0f;
+                        for (int j4 = 0; j4 < KP / 4; ++j4) {
+                            const float4 dd = dv[j4];
+                            unsigned long long p0 = mul2(pack2(a[4 * j4], a[4 * j4 + 1]), pack2(dd.x, dd.y));
+                            unsigned long long p1 = mul2(pack2(a[4 * j4 + 2], a[4 * j4 + 3]), pack2(dd.z, dd.w));
+                            unpack2(p0, a[4 * j4], a[4 * j4 + 1]);
+                            unpack2(p1, a[4 * j4 + 2], a[4 * j4 + 3]);
+                        }
+                        expo[u] += Et[u];
+                        const bool last = (t + 1 == len[u]);
+                        if ((t + 1) % renorm == 0 || last) {
+                            float m4[KP / 4];
 #pragma unroll
-                                for (int j = 0; j < KP; ++j) mx = fmaxf(mx, acc[j]);
-                                if (mx > 0.0f) {
-                                    if (!isfinite(mx)) atomicOr(status, ST_ENUMERIC);
-                                    int rr = float_exponent(mx);
-                                    rr = rr < -126 ? -126 : (rr > 126 ? 126 : rr);
-                                    const float s = pow2f(-rr);
+                            for (int j = 0; j < KP / 4; ++j) m4[j] = max3f(max3f(a[4 * j], a[4 * j + 1], a[4 * j + 2]), a[4 * j + 3], 0.0f);
 #pragma unroll
-                                    for (int j = 0; j < KP; ++j) acc[j] *= s;
-                                    expo[u] += rr;
+                            for (int s = KP / 8; s > 0; s >>= 1)
+#pragma unroll
+                                for (int j = 0; j < s; ++j) m4[j] = fmaxf(m4[j], m4[j + s]);
+                            const float mx = m4[0];
+                            if (mx > 0.0f) {
+                                if (!isfinite(mx)) atomicOr(status, ST_ENUMERIC);
+                                int rr = float_exponent(mx);
+                                rr = rr < -126 ? -126 : (rr > 126 ? 126 : rr);
+                                const unsigned long long s2 = pack2(pow2f(-rr), pow2f(-rr));
+#pragma unroll
+                                for (int j = 0; j < KP / 2; ++j) {
+                                    unsigned long long pp = mul2(pack2(a[2 * j], a[2 * j + 1]), s2);
+                                    unpack2(pp, a[2 * j], a[2 * j + 1]);
                                 }
+                                expo[u] += rr;
                             }
-                            if (!last) {
-                                // next A operand row (rounded to the operand type)
-                                const uint32_t arow = a_base + g * C::A_BYTES + (r >> 3) * C::SBO + (r & 7) * 16;
-                                if constexpr (C::ESZ == 4) {
-#pragma unroll
-                                    for (int kc = 0; kc < KP / 4; ++kc)
-                                        st_shared_v4(arow + kc * 128, to_tf32_bits(acc[4 * kc]),
-                                                     to_tf32_bits(acc[4 * kc + 1]), to_tf32_bits(acc[4 * kc + 2]),
-                                                     to_tf32_bits(acc[4 * kc + 3]));
-                                } else {
-#pragma unroll
-                                    for (int kc = 0; kc < KP / 8; ++kc) {
-                                        uint32_t w4[4];
-#pragma unroll
-                                        for (int h = 0; h < 4; ++h) {
-                                            __nv_bfloat162 bb = __floats2bfloat162_rn(acc[8 * kc + 2 * h], acc[8 * kc + 2 * h + 1]);
-                                            w4[h] = *reinterpret_cast<uint32_t *>(&bb);
-                                        }
-                                        st_shared_v4(arow + kc * 128, w4[0], w4[1], w4[2], w4[3]);
-                                    }
-                                }
-                                fence_proxy_async_smem();
-                            } else {
-                                float mx = 0.0f;
-#pragma unroll
-                                for (int j = 0; j < KP; ++j) mx = fmaxf(mx, acc[j]);
-                                const size_t j = (size_t)q * n_chunks + jchunk[u];
-                                float4 *dst = reinterpret_cast<float4 *>(A0 + j * KP * KP + (size_t)i * KP);
+                            if (last) {
+                                const size_t jj = (size_t)q * n_chunks + (size_t)b * per_item + (team + E * u) * C::CPG + cs;
+                                float4 *dst = reinterpret_cast<float4 *>(A0 + jj * KP * KP + (size_t)i * KP);
 #pragma unroll
                                 for (int j4 = 0; j4 < KP / 4; ++j4)
-                                    dst[j4] = make_float4(acc[4 * j4], acc[4 * j4 + 1], acc[4 * j4 + 2], acc[4 * j4 + 3]);
-                                e0[j * KP + i] = (mx > 0.0f) ? expo[u] : ZERO_ROW_EXP32;
+                                    dst[j4] = make_float4(a[4 * j4], a[4 * j4 + 1], a[4 * j4 + 2], a[4 * j4 + 3]);
+                                e0[jj * KP + i] = (mx > 0.0f) ? expo[u] : ZERO_ROW_EXP32;
                             }
                         }
-                        tc_fence_before();
                     }
+                    // next A operand row, rounded to the operand type, into TMEM. The
+                    // store is warp-wide: rows whose chunk has ended (or ends now) write
+                    // whatever they hold, which only ever feeds their own ignored rows.
+                    if (okw && __any_sync(0xffffffffu, t + 1 < len[u])) {
+                        uint32_t *w = reinterpret_cast<uint32_t *>(a);  // converted in place
+                        if constexpr (C::ESZ == 4) {
+#pragma unroll
+                            for (int c = 0; c < KP; ++c) w[c] = to_tf32_bits(a[c]);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < KP / 2; ++c) {
+                                __nv_bfloat162 bb = __floats2bfloat162_rn(a[2 * c], a[2 * c + 1]);
+                                w[c] = *reinterpret_cast<uint32_t *>(&bb);
+                            }
+                        }
+                        tmem_st_row<C::KA>(tm_row + C::A_COL0 + g * C::KA, w);
+                        tmem_wait_st();
+                    }
+                    tc_fence_before();
                     __syncwarp();
                     if (t + 1 < steps && lane == 0) mbar_arrive(&empty[g]);
                 }
             }
+            cp_async_wait0();
         }
         // a bulk copy that was issued but never consumed must land before exit
         if (ew == 0 && lane == 0 && pload_issued) {
@@ -535,6 +664,7 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, int K, ConstLayout lay,
             while (!mbar_try_wait(pload, (pload_issued - 1) & 1u) && clock64() - t0 < SPIN_LIMIT_CYCLES) {
             }
         }
+        cp_async_wait0();
     }
     tc_fence_before();
     __syncthreads();
@@ -546,9 +676,9 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, int K, ConstLayout lay,
 }
 
 template <int KP, int PREC, int G, int E>
-cudaError_t launch_tc_t(int n_prop, int n_chunks, int renorm, int K, const ConstLayout &lay,
-                        const float *cblock, const ChunkDesc *chunks, const float2 *packed, float *A0,
-                        int32_t *e0, unsigned *status, cudaStream_t st) {
+cudaError_t launch_tc_t(int n_prop, int n_chunks, int renorm, const ConstLayout &lay, const float *cblock,
+                        const ChunkDesc *chunks, const float2 *packed, float *A0, int32_t *e0, unsigned *status,
+                        cudaStream_t st) {
     using C = TcCfg<KP, PREC, G, E>;
     auto kern = chunk_tc_kernel<KP, PREC, G, E>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
@@ -559,10 +689,19 @@ cudaError_t launch_tc_t(int n_prop, int n_chunks, int renorm, int K, const Const
     const int per_item = G * C::CPG;
     const long long n_items = (long long)n_prop * ((n_chunks + per_item - 1) / per_item);
     const int grid = (int)(n_items < sms ? n_items : sms);
-    kern<<<grid, C::THREADS, C::SMEM, st>>>(n_prop, n_chunks, renorm, K, lay, cblock, chunks, packed, A0, e0,
-                                             status);
+    kern<<<grid, C::THREADS, C::SMEM, st>>>(n_prop, n_chunks, renorm, lay, cblock, chunks, packed, A0, e0, status);
     return cudaGetLastError();
 }
+
+// tile configuration per (KP, precision): groups in flight G, epilogue teams E
+template <int KP, int PREC>
+struct TcTile;
+template <> struct TcTile<32, HMM_PREC_TF32> { static constexpr int G = 8, E = 4; };
+template <> struct TcTile<32, HMM_PREC_TF32_SPLIT> { static constexpr int G = 8, E = 4; };
+template <> struct TcTile<32, HMM_PREC_BF16> { static constexpr int G = 8, E = 4; };
+template <> struct TcTile<16, HMM_PREC_TF32> { static constexpr int G = 16, E = 4; };
+template <> struct TcTile<16, HMM_PREC_TF32_SPLIT> { static constexpr int G = 16, E = 4; };
+template <> struct TcTile<16, HMM_PREC_BF16> { static constexpr int G = 16, E = 4; };
 
 }  // namespace
 
@@ -571,7 +710,18 @@ bool chunk_tc_supported(int K, int precision) {
     return K >= 1 && K <= 32;
 }
 
-int chunk_tc_chunks_per_item(int KP) { return 8 * (TC_M / KP); }
+int chunk_tc_chunks_per_item(int KP, int precision) {
+#define HMM_TC_PER_ITEM(KPV, PRECV) \
+    if (KP == KPV && precision == PRECV) return TcTile<KPV, PRECV>::G * (TC_M / KPV);
+    HMM_TC_PER_ITEM(16, HMM_PREC_TF32)
+    HMM_TC_PER_ITEM(32, HMM_PREC_TF32)
+    HMM_TC_PER_ITEM(16, HMM_PREC_TF32_SPLIT)
+    HMM_TC_PER_ITEM(32, HMM_PREC_TF32_SPLIT)
+    HMM_TC_PER_ITEM(16, HMM_PREC_BF16)
+    HMM_TC_PER_ITEM(32, HMM_PREC_BF16)
+#undef HMM_TC_PER_ITEM
+    return 32;
+}
 
 cudaError_t launch_chunk_tc(int n_prop, int n_chunks, int L, int renorm, int precision,
                             const ConstLayout &lay, const float *cblock, const ChunkDesc *chunks,
@@ -579,11 +729,11 @@ cudaError_t launch_chunk_tc(int n_prop, int n_chunks, int L, int renorm, int pre
                             cudaStream_t st) {
     (void)L;
     if (n_chunks == 0 || n_prop == 0) return cudaSuccess;
-    const int K = 0;
-#define HMM_TC_CASE(KPV, PRECV)                                                                    \
-    if (lay.KP == KPV && precision == PRECV)                                                        \
-        return launch_tc_t<KPV, PRECV, 8, 2>(n_prop, n_chunks, renorm, K, lay, cblock, chunks, packed, \
-                                              A0, e0, status, st);
+#define HMM_TC_CASE(KPV, PRECV)                                                                              \
+    if (lay.KP == KPV && precision == PRECV)                                                                  \
+        return launch_tc_t<KPV, PRECV, TcTile<KPV, PRECV>::G, TcTile<KPV, PRECV>::E>(n_prop, n_chunks, renorm, \
+                                                                                   lay, cblock, chunks,       \
+                                                                                   packed, A0, e0, status, st);
     HMM_TC_CASE(16, HMM_PREC_TF32)
     HMM_TC_CASE(32, HMM_PREC_TF32)
     HMM_TC_CASE(16, HMM_PREC_TF32_SPLIT)

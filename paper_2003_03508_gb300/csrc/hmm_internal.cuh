@@ -18,7 +18,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/hmm_gb300.h"
+#include "hmm_gb300.h"
 
 namespace hmm {
 
@@ -134,7 +134,7 @@ cudaError_t launch_chunk_simt(int n_prop, int n_chunks, int L, int renorm, const
                               float *A0, int32_t *e0, unsigned *status, cudaStream_t st);
 
 bool chunk_tc_supported(int K, int precision);
-int chunk_tc_chunks_per_item(int KP);
+int chunk_tc_chunks_per_item(int KP, int precision);
 cudaError_t launch_chunk_tc(int n_prop, int n_chunks, int L, int renorm, int precision,
                             const ConstLayout &lay, const float *cblock, const ChunkDesc *chunks,
                             const float2 *packed, float *A0, int32_t *e0, unsigned *status,
