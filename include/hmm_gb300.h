@@ -185,6 +185,39 @@ int hmm_profile_enable(hmm_ctx *ctx, int on);
  */
 int hmm_profile_read(hmm_ctx *ctx, double *ms_out, int *n_calls);
 
+/* ---- allocation-free variant ---- */
+#define HMM_NOALLOC_MAX_K 32             /* largest state count it accepts  */
+#define HMM_NOALLOC_MAX_T (1LL << 20)    /* longest sequence it accepts     */
+
+/*
+ * hmm_loglik without any device allocation (the paper has no counterpart:
+ * this is a library concern).
+ *
+ * For callers that cannot allocate device memory during the call: code that
+ * runs inside a framework owning every allocation, services whose device
+ * footprint must stay fixed, or code that must not risk the implicit device
+ * synchronisation cudaMalloc/cudaFree can cause. There is no context: the
+ * scratch space (about 13 MiB) is one file-scope __device__ array, created
+ * when the library is loaded and held by every GPU that loads it until the
+ * process exits. The caller passes inputs and output as for hmm_loglik.
+ *
+ * Computes what hmm_loglik computes with default options (FP32-SIMT chunk
+ * products, emit-first convention, chunk length 1024, renormalisation every
+ * 4 steps), for 1 <= K <= HMM_NOALLOC_MAX_K and 0 <= T <= HMM_NOALLOC_MAX_T;
+ * anything larger is rejected with HMM_EINVAL before any work is queued.
+ * out_dev: device pointer to one double. Invalid parameter data (checked on
+ * the device) gives NaN; a true zero likelihood gives -INFINITY.
+ *
+ * The first call on each device looks the scratch address up (with that
+ * device current), so make it before any stream capture. Every call reuses
+ * the same scratch and leaves its contents behind (the parts that must start
+ * at zero are cleared on `stream`). Calls that overlap on the GPU race on
+ * the scratch: order them (one stream) or use hmm_loglik with a context.
+ * Returns HMM_OK, HMM_EINVAL (bad arguments or sizes) or HMM_ECUDA.
+ */
+int hmm_loglik_noalloc(const hmm_params *params, const hmm_obs *obs, double *out_dev,
+                       void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,6 +80,7 @@ SIGNATURES = {
                                                _VP, _VP, _VP, ctypes.POINTER(hmm_opts), _VP, _VP]),
     "hmm_last_launch_count": (ctypes.c_int, [_VP]),
     "hmm_last_chunk_len": (ctypes.c_int, [_VP]),
+    "hmm_loglik_noalloc": (ctypes.c_int, [ctypes.POINTER(hmm_params), ctypes.POINTER(hmm_obs), _VP, _VP]),
     "hmm_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "hmm_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int)]),
@@ -251,6 +252,28 @@ class Context:
             self.h, n_prop, K, *ptrs[:5], int(offs.shape[0] - 1), offs.ctypes.data, ptrs[5],
             ptrs[6], ctypes.byref(o), optr, _stream_ptr(stream)))
         return out
+
+
+def hmm_loglik_noalloc(pi, P, p_tremor, mu, cov, xy, tremor, out=None, stream=None):
+    """log L through the allocation-free entry point (no context; fixed scratch).
+
+    Same arguments as Context.hmm_loglik without options; K <= 32, T <= 2^20.
+    """
+    for t, n in ((pi, "pi"), (P, "P"), (p_tremor, "p_tremor"), (mu, "mu"), (cov, "cov")):
+        _dev(t, torch.float32, n)
+    _dev(xy, torch.float32, "xy")
+    _dev(tremor, torch.uint8, "tremor")
+    K = int(pi.shape[0])
+    T = int(tremor.shape[0])
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=pi.device)
+    prm = hmm_params(K, pi.data_ptr(), P.data_ptr(), p_tremor.data_ptr(), mu.data_ptr(), cov.data_ptr())
+    ob = hmm_obs(T, xy.data_ptr() if T else None, tremor.data_ptr() if T else None)
+    rc = load_library().hmm_loglik_noalloc(ctypes.byref(prm), ctypes.byref(ob), out.data_ptr(),
+                                           _stream_ptr(stream))
+    if rc != HMM_OK:
+        raise HMMError(rc, "hmm_loglik_noalloc rejected the call")
+    return out
 
 
 _default_ctx = {}
