@@ -80,9 +80,74 @@ def _declare(L):
         _declare_mcmc(L)
 
 
+class OraclePrior(ctypes.Structure):
+    """Mirror of the oracle's prior settings (see mcmc_oracle.c)."""
+    _fields_ = [("alpha_P", ctypes.c_double), ("alpha_pi", ctypes.c_double),
+                ("p_mean_lo", ctypes.c_double), ("p_mean_hi", ctypes.c_double),
+                ("p_var", ctypes.c_double), ("box", ctypes.c_double * 4),
+                ("iw_df", ctypes.c_double)]
+
+
 def _declare_mcmc(L):
     L.oracle_philox4x32_10.argtypes = [_u32, _u32, _u32]
     L.oracle_philox4x32_10.restype = None
+    L.oracle_normal.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                ctypes.c_uint32]
+    L.oracle_normal.restype = ctypes.c_double
+    L.oracle_uniform.argtypes = L.oracle_normal.argtypes
+    L.oracle_uniform.restype = ctypes.c_double
+    L.oracle_theta_dim.argtypes = [ctypes.c_int]
+    L.oracle_theta_dim.restype = ctypes.c_int
+    L.oracle_theta_to_params.argtypes = [ctypes.c_int, _d, ctypes.POINTER(OraclePrior), _d, _d, _d, _d, _d]
+    L.oracle_theta_to_params.restype = ctypes.c_double
+
+
+def default_prior(K, box=(0.0, 300.0, 0.0, 150.0)):
+    """The prior settings read from Section "Model priors" and Appendix A."""
+    return dict(alpha_P=0.01, alpha_pi=1.0, p_mean_lo=0.1, p_mean_hi=0.9, p_var=0.001,
+                box=tuple(box), iw_df=float(K))
+
+
+def _prior_struct(prior):
+    pr = OraclePrior()
+    for k, v in prior.items():
+        if k == "box":
+            pr.box = (ctypes.c_double * 4)(*v)
+        else:
+            setattr(pr, k, float(v))
+    return pr
+
+
+def philox4x32_10(ctr, key):
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
+    out = np.zeros(4, dtype=np.uint32)
+    lib().oracle_philox4x32_10(c.ctypes.data_as(_u32), k.ctypes.data_as(_u32), out.ctypes.data_as(_u32))
+    return out
+
+
+def normal(seed, stream, chain, it, index):
+    return lib().oracle_normal(int(seed), int(stream), int(chain), int(it), int(index))
+
+
+def uniform(seed, stream, chain, it, index):
+    return lib().oracle_uniform(int(seed), int(stream), int(chain), int(it), int(index))
+
+
+def theta_dim(K):
+    return int(lib().oracle_theta_dim(int(K)))
+
+
+def theta_to_params(theta, K, prior):
+    """theta -> (pi, P, p, mu, cov) in float64 and log prior + log Jacobian."""
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+    assert th.shape == (theta_dim(K),)
+    pi = np.zeros(K); P = np.zeros(K * K); p = np.zeros(K); mu = np.zeros(2 * K); cov = np.zeros(3 * K)
+    pr = _prior_struct(prior)
+    lp = lib().oracle_theta_to_params(int(K), th.ctypes.data_as(_d), ctypes.byref(pr), pi.ctypes.data_as(_d),
+                                      P.ctypes.data_as(_d), p.ctypes.data_as(_d), mu.ctypes.data_as(_d),
+                                      cov.ctypes.data_as(_d))
+    return (pi, P.reshape(K, K), p, mu.reshape(K, 2), cov.reshape(K, 3)), lp
 
 
 def compile_variant(source_text: str, out_dir) -> ctypes.CDLL:

@@ -41,7 +41,9 @@ def _digest(extra=()) -> str:
     for p in sorted(list(CSRC.glob("*.cu")) + list(CSRC.glob("*.cuh")) + list(INCLUDE.glob("*.h"))):
         h.update(p.name.encode())
         h.update(p.read_bytes())
-    h.update(" ".join(ARCH + NVCC_FLAGS + list(extra)).encode())
+    # flags without the (machine-dependent) include path, so every machine
+    # that builds the same sources gets the same library name
+    h.update(" ".join(f for f in ARCH + NVCC_FLAGS + list(extra) if not f.startswith("-I")).encode())
     return h.hexdigest()[:12]
 
 
