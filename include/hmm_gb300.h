@@ -185,6 +185,94 @@ int hmm_profile_enable(hmm_ctx *ctx, int on);
  */
 int hmm_profile_read(hmm_ctx *ctx, double *ms_out, int *n_calls);
 
+/* ---- Bayesian fitting: random-walk Metropolis-Hastings (Section "Monte Carlo Markov Chains") ---- */
+
+/*
+ * Prior settings (Section "Model priors", Appendix A, as read here):
+ * Dirichlet(alpha_P) on every row of P, Dirichlet(alpha_pi) on pi,
+ * Gamma(shape m^2/v, rate m/v) truncated to (0,1) on p_k with m = p_mean_lo
+ * for k < K/2 and p_mean_hi otherwise, v = p_var; means uniform on the box
+ * [box[0], box[1]] x [box[2], box[3]]; Sigma_k inverse-Wishart(iw_df, I_2).
+ */
+typedef struct {
+    float alpha_P, alpha_pi;
+    float p_mean_lo, p_mean_hi, p_var;
+    float box[4];
+    float iw_df;
+} hmm_prior;
+
+/* alpha_P = 0.01, alpha_pi = 1, means 0.1 / 0.9, variance 0.001, box [0,300]x[0,150] km, df = K */
+void hmm_prior_default(hmm_prior *prior, int32_t K);
+
+/*
+ * Dimension of the unconstrained state theta for K states: K^2 + 6K - 1.
+ * Layout: K(K-1) reference logits of the rows of P (row i, columns j != i,
+ * the diagonal being the reference), K-1 reference logits of pi (state 0 the
+ * reference), K logits of p_k, 2K means (x, y), 2K (log sigma_x, log
+ * sigma_y), K atanh(rho).
+ */
+int32_t hmm_theta_dim(int32_t K);
+
+/*
+ * theta [n][D] (device, float) -> parameters in the layout hmm_loglik_batched
+ * takes (device, float) and logprior[n] (device, double) = log prior density
+ * + log Jacobian of the map (up to a theta-independent constant; -INFINITY
+ * when a mean lies outside the box). prior may be NULL (defaults). 2 <= K <= 80.
+ */
+int hmm_theta_to_params(int32_t n, int32_t K, const float *theta, const hmm_prior *prior, float *pi,
+                        float *P, float *p_tremor, float *mu, float *cov, double *logprior, void *stream);
+
+typedef struct hmm_sampler hmm_sampler;
+
+/*
+ * n_chains independent random-walk Metropolis-Hastings chains on one GPU.
+ * theta0: device [n_chains][D] starting states; step: device [D] proposal
+ * standard deviations (theta' = theta + step * N(0, I)); seed keys the
+ * Philox4x32-10 counter-based generator. The observations (device, as for
+ * hmm_loglik_batched; seg_offsets is a host array and is copied) must stay
+ * valid while the sampler lives. opts selects the likelihood precision; with
+ * opts->recheck_fp32 != 0 and a tensor-core precision, every hmm_mcmc_step
+ * call ends by re-evaluating the current states with FP32-SIMT chunk
+ * products, so the stored log likelihoods are FP32 ones. The sampler owns
+ * its device state and two private contexts on `device`.
+ */
+int hmm_sampler_create(hmm_sampler **sampler, int device, int32_t n_chains, int32_t K,
+                       const hmm_prior *prior, const float *theta0, const float *step, uint64_t seed,
+                       int32_t n_seg, const int64_t *seg_offsets, const float *xy,
+                       const uint8_t *tremor, const hmm_opts *opts, void *stream);
+
+int hmm_sampler_destroy(hmm_sampler *sampler);
+
+/*
+ * n_iter iterations of every chain: propose, evaluate the batched likelihood
+ * of all proposals, accept or reject (log u < log posterior ratio, u from
+ * Philox). After the first iteration the sampler runs each iteration as one
+ * CUDA graph replay. trace_logpost (device [n_iter][n_chains] float) and
+ * trace_theta (device [n_iter][n_chains][D] float) receive the state after
+ * each iteration when not NULL. Asynchronous on `stream`, except for a short
+ * synchronisation at the start of the call.
+ */
+int hmm_mcmc_step(hmm_sampler *sampler, int32_t n_iter, float *trace_logpost, float *trace_theta,
+                  void *stream);
+
+/* Re-evaluate every chain's current state with FP32-SIMT chunk products
+ * (the reported log likelihood becomes the FP32 one); *max_abs_change_dev
+ * (device double, may be NULL) receives the largest change. */
+int hmm_sampler_recheck(hmm_sampler *sampler, double *max_abs_change_dev, void *stream);
+
+/* Copy the current states: theta [n_chains][D] (float), log posterior,
+ * log likelihood (double), accepted-proposal counts (uint64); all device
+ * pointers, each may be NULL. */
+int hmm_sampler_state(hmm_sampler *sampler, float *theta_out, double *logpost_out, double *loglik_out,
+                      unsigned long long *n_accept_out, void *stream);
+
+/* Kernel launches per iteration (the CUDA graph's node count of kernels). */
+int hmm_sampler_launches_per_iter(const hmm_sampler *sampler);
+
+/* 1 when iterations replay a captured CUDA graph, 0 when they are launched
+ * directly (before the second iteration, or if capture failed). */
+int hmm_sampler_graph_active(const hmm_sampler *sampler);
+
 /* ---- allocation-free variant ---- */
 #define HMM_NOALLOC_MAX_K 32             /* largest state count it accepts  */
 #define HMM_NOALLOC_MAX_T (1LL << 20)    /* longest sequence it accepts     */

@@ -55,6 +55,12 @@ class hmm_params(ctypes.Structure):
                 ("p_tremor", ctypes.c_void_p), ("mu", ctypes.c_void_p), ("cov", ctypes.c_void_p)]
 
 
+class hmm_prior(ctypes.Structure):
+    _fields_ = [("alpha_P", ctypes.c_float), ("alpha_pi", ctypes.c_float), ("p_mean_lo", ctypes.c_float),
+                ("p_mean_hi", ctypes.c_float), ("p_var", ctypes.c_float), ("box", ctypes.c_float * 4),
+                ("iw_df", ctypes.c_float)]
+
+
 class hmm_obs(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int64), ("xy", ctypes.c_void_p), ("tremor", ctypes.c_void_p)]
 
@@ -80,6 +86,19 @@ SIGNATURES = {
                                                _VP, _VP, _VP, ctypes.POINTER(hmm_opts), _VP, _VP]),
     "hmm_last_launch_count": (ctypes.c_int, [_VP]),
     "hmm_last_chunk_len": (ctypes.c_int, [_VP]),
+    "hmm_prior_default": (None, [ctypes.POINTER(hmm_prior), _I32]),
+    "hmm_theta_dim": (ctypes.c_int32, [_I32]),
+    "hmm_theta_to_params": (ctypes.c_int, [_I32, _I32, _VP, ctypes.POINTER(hmm_prior), _VP, _VP, _VP, _VP, _VP,
+                                           _VP, _VP]),
+    "hmm_sampler_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, _I32, _I32, ctypes.POINTER(hmm_prior),
+                                          _VP, _VP, ctypes.c_uint64, _I32, _VP, _VP, _VP,
+                                          ctypes.POINTER(hmm_opts), _VP]),
+    "hmm_sampler_destroy": (ctypes.c_int, [_VP]),
+    "hmm_mcmc_step": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP]),
+    "hmm_sampler_recheck": (ctypes.c_int, [_VP, _VP, _VP]),
+    "hmm_sampler_state": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "hmm_sampler_launches_per_iter": (ctypes.c_int, [_VP]),
+    "hmm_sampler_graph_active": (ctypes.c_int, [_VP]),
     "hmm_loglik_noalloc": (ctypes.c_int, [ctypes.POINTER(hmm_params), ctypes.POINTER(hmm_obs), _VP, _VP]),
     "hmm_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "hmm_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
@@ -274,6 +293,118 @@ def hmm_loglik_noalloc(pi, P, p_tremor, mu, cov, xy, tremor, out=None, stream=No
     if rc != HMM_OK:
         raise HMMError(rc, "hmm_loglik_noalloc rejected the call")
     return out
+
+
+def make_prior(K, **kw):
+    """hmm_prior with the library defaults for K states, fields overridden by kw."""
+    pr = hmm_prior()
+    load_library().hmm_prior_default(ctypes.byref(pr), int(K))
+    for k, v in kw.items():
+        if k == "box":
+            pr.box = (ctypes.c_float * 4)(*v)
+        else:
+            setattr(pr, k, float(v))
+    return pr
+
+
+def theta_dim(K):
+    return int(load_library().hmm_theta_dim(int(K)))
+
+
+def theta_to_params(theta, K, prior=None, stream=None):
+    """theta [n, D] CUDA float32 -> (pi, P, p_tremor, mu, cov) CUDA tensors and logprior [n] (float64)."""
+    _dev(theta, torch.float32, "theta")
+    n = int(theta.shape[0])
+    dv = theta.device
+    pi = torch.empty(n, K, device=dv)
+    P = torch.empty(n, K, K, device=dv)
+    p = torch.empty(n, K, device=dv)
+    mu = torch.empty(n, K, 2, device=dv)
+    cov = torch.empty(n, K, 3, device=dv)
+    lp = torch.empty(n, dtype=torch.float64, device=dv)
+    pr = prior if prior is not None else make_prior(K)
+    rc = load_library().hmm_theta_to_params(n, int(K), theta.data_ptr(), ctypes.byref(pr), pi.data_ptr(),
+                                            P.data_ptr(), p.data_ptr(), mu.data_ptr(), cov.data_ptr(),
+                                            lp.data_ptr(), _stream_ptr(stream))
+    if rc != HMM_OK:
+        raise HMMError(rc, "hmm_theta_to_params failed")
+    return (pi, P, p, mu, cov), lp
+
+
+class Sampler:
+    """n_chains random-walk Metropolis-Hastings chains (wraps hmm_sampler)."""
+
+    def __init__(self, K, theta0, step, seed, seg_offsets, xy, tremor, prior=None, opts=None, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the sampler has no CPU path")
+        self.lib = load_library()
+        _dev(theta0, torch.float32, "theta0")
+        _dev(step, torch.float32, "step")
+        _dev(xy, torch.float32, "xy")
+        _dev(tremor, torch.uint8, "tremor")
+        self.K, self.C, self.D = int(K), int(theta0.shape[0]), int(theta0.shape[1])
+        assert self.D == theta_dim(K) and step.shape == (self.D,)
+        self._keep = (xy, tremor)  # the sampler reads them for its whole life
+        self.offs = np.ascontiguousarray(np.asarray(seg_offsets, dtype=np.int64))
+        self.prior = prior if prior is not None else make_prior(K)
+        self.opts = opts if opts is not None else make_opts()
+        h = _VP()
+        T = int(self.offs[-1])
+        rc = self.lib.hmm_sampler_create(ctypes.byref(h), torch.cuda.current_device(), self.C, self.K,
+                                         ctypes.byref(self.prior), theta0.data_ptr(), step.data_ptr(),
+                                         int(seed), int(self.offs.shape[0] - 1), self.offs.ctypes.data,
+                                         xy.data_ptr() if T else None, tremor.data_ptr() if T else None,
+                                         ctypes.byref(self.opts), _stream_ptr(stream))
+        if rc != HMM_OK:
+            raise HMMError(rc, "hmm_sampler_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hmm_sampler_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n_iter, trace_logpost=False, trace_theta=False, stream=None):
+        """Run n_iter iterations; returns (logpost trace [n, C], theta trace [n, C, D]) or Nones."""
+        lp = torch.empty(n_iter, self.C, device="cuda") if trace_logpost else None
+        th = torch.empty(n_iter, self.C, self.D, device="cuda") if trace_theta else None
+        rc = self.lib.hmm_mcmc_step(self.h, int(n_iter), lp.data_ptr() if lp is not None else None,
+                                    th.data_ptr() if th is not None else None, _stream_ptr(stream))
+        if rc != HMM_OK:
+            raise HMMError(rc, "hmm_mcmc_step failed")
+        return lp, th
+
+    def recheck(self, stream=None):
+        d = torch.empty(1, dtype=torch.float64, device="cuda")
+        rc = self.lib.hmm_sampler_recheck(self.h, d.data_ptr(), _stream_ptr(stream))
+        if rc != HMM_OK:
+            raise HMMError(rc, "hmm_sampler_recheck failed")
+        return d
+
+    def state(self, stream=None):
+        th = torch.empty(self.C, self.D, device="cuda")
+        lp = torch.empty(self.C, dtype=torch.float64, device="cuda")
+        ll = torch.empty(self.C, dtype=torch.float64, device="cuda")
+        na = torch.empty(self.C, dtype=torch.int64, device="cuda")
+        rc = self.lib.hmm_sampler_state(self.h, th.data_ptr(), lp.data_ptr(), ll.data_ptr(), na.data_ptr(),
+                                        _stream_ptr(stream))
+        if rc != HMM_OK:
+            raise HMMError(rc, "hmm_sampler_state failed")
+        return th, lp, ll, na
+
+    @property
+    def launches_per_iter(self):
+        return int(self.lib.hmm_sampler_launches_per_iter(self.h))
+
+    @property
+    def graph_active(self):
+        return bool(self.lib.hmm_sampler_graph_active(self.h))
 
 
 _default_ctx = {}

@@ -1,0 +1,606 @@
+// Random-walk Metropolis-Hastings over the batched likelihood (hmm_mcmc_step).
+//
+// Section "Monte Carlo Markov Chains": a proposed state is accepted with
+// probability min(1, likelihood x prior ratio). Section "Model priors" and
+// Appendix A give the priors; they are read as: Dirichlet(alpha_P) on every
+// row of P, Dirichlet(alpha_pi) on pi, Gamma(m^2/v, m/v) on p_k truncated to
+// (0,1) (m = p_mean_lo for k < K/2, else p_mean_hi), 2x2 inverse-Wishart
+// (df = iw_df, scale I) on Sigma_k, and uniform means on a box.
+//
+// The chains move in unconstrained coordinates theta (dimension K^2+6K-1):
+// reference-logit rows of P (the diagonal is the reference), reference-logit
+// pi (state 0 is the reference), logit p_k, the means, log sigma_x, log
+// sigma_y, atanh rho. The log density of theta is the log prior plus the log
+// Jacobian of theta -> parameters, evaluated in FP64.
+//
+// Random numbers are Philox4x32-10 (Salmon et al., SC 2011) keyed by the seed
+// with counter (index/2, chain, iteration, 0) for the proposal normals
+// (Box-Muller, cos/sin) and (index, chain, iteration, 1) for the acceptance
+// uniform, so a run is reproducible and any draw can be recomputed.
+//
+// One iteration = propose (+ transform) kernel, the batched likelihood, the
+// accept kernel, and a one-thread kernel that advances the iteration counter
+// kept in device memory. After a first, ordinary iteration the sampler
+// captures one iteration in a CUDA graph and replays it.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "hmm_internal.cuh"
+
+namespace hmm {
+namespace mcmc {
+
+constexpr uint32_t PH_M0 = 0xD2511F53u, PH_M1 = 0xCD9E8D57u, PH_W0 = 0x9E3779B9u, PH_W1 = 0xBB67AE85u;
+
+__device__ __forceinline__ void philox(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += PH_W0;
+            k1 += PH_W1;
+        }
+        const uint32_t hi0 = __umulhi(PH_M0, c[0]), lo0 = PH_M0 * c[0];
+        const uint32_t hi1 = __umulhi(PH_M1, c[2]), lo1 = PH_M1 * c[2];
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+
+__device__ __forceinline__ double u01(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0) + (1.0 / 33554432.0); }
+
+__device__ double normal_draw(uint64_t seed, uint32_t chain, uint32_t iter, uint32_t index) {
+    uint32_t c[4] = {index / 2, chain, iter, 0u};
+    philox(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const double rad = sqrt(-2.0 * log(u01(c[0])));
+    const double ang = 6.283185307179586476925286766559 * u01(c[1]);
+    return (index & 1) ? rad * sin(ang) : rad * cos(ang);
+}
+
+__device__ double uniform_draw(uint64_t seed, uint32_t chain, uint32_t iter, uint32_t index) {
+    uint32_t c[4] = {index, chain, iter, 1u};
+    philox(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    return u01(c[0]);
+}
+
+struct Prior {
+    double alpha_P, alpha_pi, p_mean_lo, p_mean_hi, p_var, box[4], iw_df;
+};
+
+constexpr int TPB = 128;
+
+__device__ double block_sum(double v, double *red) {
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = TPB / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// theta (one chain, FP64 values in shared memory) -> parameters (FP32, the
+// batched likelihood's layout) and the log density of theta. One CTA.
+__device__ double transform(int K, const double *th, const Prior &pr, float *pi, float *P, float *p, float *mu,
+                            float *cov, double *red) {
+    double part = 0.0;
+    // rows of P
+    for (int i = threadIdx.x; i < K; i += TPB) {
+        const double *z = th + (size_t)i * (K - 1);
+        double mx = 0.0;
+        for (int q = 0; q < K - 1; ++q) mx = fmax(mx, z[q]);
+        double s = exp(-mx);
+        for (int q = 0; q < K - 1; ++q) s += exp(z[q] - mx);
+        const double lse = mx + log(s);
+        for (int j = 0, q = 0; j < K; ++j) {
+            const double zz = (j == i) ? 0.0 : z[q++];
+            P[(size_t)i * K + j] = (float)exp(zz - lse);
+            part += pr.alpha_P * (zz - lse);
+        }
+    }
+    int o = K * (K - 1);
+    // pi
+    if (threadIdx.x == 0) {
+        double mx = 0.0;
+        for (int k = 1; k < K; ++k) mx = fmax(mx, th[o + k - 1]);
+        double s = exp(-mx);
+        for (int k = 1; k < K; ++k) s += exp(th[o + k - 1] - mx);
+        const double lse = mx + log(s);
+        for (int k = 0; k < K; ++k) {
+            const double zz = k == 0 ? 0.0 : th[o + k - 1];
+            pi[k] = (float)exp(zz - lse);
+            part += pr.alpha_pi * (zz - lse);
+        }
+    }
+    o += K - 1;
+    for (int k = threadIdx.x; k < K; k += TPB) {
+        // p_k: logistic; truncated Gamma times the Jacobian p (1 - p)
+        const double w = th[o + k];
+        const double m = (k < K / 2) ? pr.p_mean_lo : pr.p_mean_hi;
+        const double a = m * m / pr.p_var, b = m / pr.p_var;
+        const double pk = 1.0 / (1.0 + exp(-w));
+        p[k] = (float)pk;
+        part += a * (-log1p(exp(-w))) - b * pk + (-log1p(exp(w)));
+        // mean: uniform on the box
+        const double x = th[o + K + 2 * k], y = th[o + K + 2 * k + 1];
+        mu[2 * k] = (float)x;
+        mu[2 * k + 1] = (float)y;
+        if (x < pr.box[0] || x > pr.box[1] || y < pr.box[2] || y > pr.box[3]) part = -INFINITY;
+        // covariance: inverse-Wishart(df, I) times the Jacobian 4 (1-rho^2) sx^3 sy^3
+        const int oc = o + 3 * K;
+        const double u = th[oc + 2 * k], v = th[oc + 2 * k + 1], r = th[oc + 2 * K + k];
+        const double sx = exp(u), sy = exp(v), rho = tanh(r);
+        const double sxx = sx * sx, syy = sy * sy, sxy = rho * sx * sy;
+        cov[3 * k] = (float)sxx;
+        cov[3 * k + 1] = (float)sxy;
+        cov[3 * k + 2] = (float)syy;
+        const double det = sxx * syy - sxy * sxy;
+        part += -0.5 * (pr.iw_df + 3.0) * log(det) - 0.5 * (sxx + syy) / det;
+        part += log(4.0) + log1p(-rho * rho) + 3.0 * u + 3.0 * v;
+    }
+    return block_sum(part, red);
+}
+
+struct Ctl {
+    unsigned long long iter;   // absolute iteration counter
+    unsigned long long iter0;  // counter at the start of the current hmm_mcmc_step call
+    float *trace_lp;           // [n][C] log posterior trace of the current call, or null
+    float *trace_theta;        // [n][C][D] state trace of the current call, or null
+};
+
+// theta -> parameters + log density, no proposal (initialisation / tests)
+__global__ void __launch_bounds__(TPB) transform_kernel(int K, int D, const float *__restrict__ theta, Prior pr,
+                                                        float *pi, float *P, float *p, float *mu, float *cov,
+                                                        double *logprior) {
+    extern __shared__ double sm[];
+    double *th = sm;
+    double *red = sm + D;
+    const int c = blockIdx.x;
+    for (int d = threadIdx.x; d < D; d += TPB) th[d] = theta[(size_t)c * D + d];
+    __syncthreads();
+    const double lp = transform(K, th, pr, pi + (size_t)c * K, P + (size_t)c * K * K, p + (size_t)c * K,
+                                mu + (size_t)c * 2 * K, cov + (size_t)c * 3 * K, red);
+    if (threadIdx.x == 0) logprior[c] = lp;
+}
+
+// theta' = theta + step * N(0, 1) (Philox), then theta' -> parameters + log density
+__global__ void __launch_bounds__(TPB) propose_kernel(int K, int D, const float *__restrict__ theta,
+                                                      const float *__restrict__ step, uint64_t seed,
+                                                      const Ctl *__restrict__ ctl, Prior pr, float *theta_prop,
+                                                      float *pi, float *P, float *p, float *mu, float *cov,
+                                                      double *logprior) {
+    extern __shared__ double sm[];
+    double *th = sm;
+    double *red = sm + D;
+    const int c = blockIdx.x;
+    const uint32_t it = (uint32_t)ctl->iter;
+    for (int d = threadIdx.x; d < D; d += TPB) {
+        const double z = normal_draw(seed, (uint32_t)c, it, (uint32_t)d);
+        const float v = (float)((double)theta[(size_t)c * D + d] + (double)step[d] * z);
+        theta_prop[(size_t)c * D + d] = v;
+        th[d] = v;
+    }
+    __syncthreads();
+    const double lp = transform(K, th, pr, pi + (size_t)c * K, P + (size_t)c * K * K, p + (size_t)c * K,
+                                mu + (size_t)c * 2 * K, cov + (size_t)c * 3 * K, red);
+    if (threadIdx.x == 0) logprior[c] = lp;
+}
+
+// Metropolis-Hastings decision: accept when log u < (log L' + log pi') -
+// (log L + log pi) + qcorr (qcorr = log q(theta|theta') - log q(theta'|theta),
+// zero for the symmetric random walk).
+__global__ void __launch_bounds__(TPB) accept_kernel(int D, uint64_t seed, const Ctl *__restrict__ ctl, float *theta,
+                                                     const float *__restrict__ theta_prop, double *logpost,
+                                                     double *loglik, double *logprior,
+                                                     const double *__restrict__ loglik_prop,
+                                                     const double *__restrict__ logprior_prop,
+                                                     const double *__restrict__ qcorr,
+                                                     unsigned long long *n_acc) {
+    const int c = blockIdx.x;
+    const uint32_t it = (uint32_t)ctl->iter;
+    __shared__ int acc;
+    if (threadIdx.x == 0) {
+        const double lpp = loglik_prop[c] + logprior_prop[c];
+        const double la = lpp - logpost[c] + (qcorr ? qcorr[c] : 0.0);
+        const double u = uniform_draw(seed, (uint32_t)c, it, 0u);
+        acc = (!isnan(lpp) && lpp > -INFINITY && log(u) < la) ? 1 : 0;
+        if (acc) {
+            logpost[c] = lpp;
+            loglik[c] = loglik_prop[c];
+            logprior[c] = logprior_prop[c];
+            n_acc[c] += 1;
+        }
+    }
+    __syncthreads();
+    if (acc)
+        for (int d = threadIdx.x; d < D; d += TPB) theta[(size_t)c * D + d] = theta_prop[(size_t)c * D + d];
+    __syncthreads();
+    const unsigned long long k = ctl->iter - ctl->iter0;
+    if (ctl->trace_lp && threadIdx.x == 0) ctl->trace_lp[k * gridDim.x + c] = (float)logpost[c];
+    if (ctl->trace_theta)
+        for (int d = threadIdx.x; d < D; d += TPB)
+            ctl->trace_theta[(k * gridDim.x + c) * D + d] = theta[(size_t)c * D + d];
+}
+
+__global__ void advance_kernel(Ctl *ctl) { ctl->iter += 1; }
+
+// replace the stored log likelihood of every chain by its FP32-SIMT value and
+// record the largest change
+__global__ void recheck_kernel(int C, const double *ll32, double *loglik, double *logpost, const double *logprior,
+                               double *maxdiff) {
+    __shared__ double red[128];
+    double m = 0.0;
+    for (int c = threadIdx.x; c < C; c += 128) {
+        const double d = fabs(ll32[c] - loglik[c]);
+        if (!isnan(d)) m = fmax(m, d);
+        loglik[c] = ll32[c];
+        logpost[c] = ll32[c] + logprior[c];
+    }
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = 64; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *maxdiff = red[0];
+}
+
+__global__ void sum_kernel(int C, const double *a, const double *b, double *out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < C) out[c] = a[c] + b[c];
+}
+
+}  // namespace mcmc
+}  // namespace hmm
+
+using namespace hmm;
+using namespace hmm::mcmc;
+
+struct hmm_sampler {
+    hmm_ctx *lik = nullptr;  // private context: its workspace never moves under the graph
+    hmm_ctx *lik32 = nullptr;  // FP32-SIMT recheck of the current states (own workspace)
+    double *loglik32 = nullptr;
+    double *recheck_maxdiff = nullptr;
+    int C = 0, K = 0, D = 0;
+    uint64_t seed = 0;
+    Prior prior{};
+    hmm_opts opts{};
+    int n_seg = 0;
+    int64_t *offs = nullptr;  // host copy
+    const float *xy = nullptr;
+    const uint8_t *tremor = nullptr;
+    // device state
+    float *theta = nullptr, *theta_prop = nullptr, *step = nullptr;
+    float *pi = nullptr, *P = nullptr, *p = nullptr, *mu = nullptr, *cov = nullptr;
+    double *logpost = nullptr, *loglik = nullptr, *logprior = nullptr, *loglik_prop = nullptr,
+           *logprior_prop = nullptr;
+    unsigned long long *n_acc = nullptr;
+    Ctl *ctl = nullptr;
+    unsigned long long iter_host = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int launches_per_iter = 0;
+    int graph_failed = 0;
+    // iterations run on the sampler's own stream (the legacy default stream
+    // cannot be captured), ordered against the caller's stream by events
+    cudaStream_t own = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+};
+
+static Prior to_prior(const hmm_prior *p, int K) {
+    Prior r{};
+    if (p) {
+        r.alpha_P = p->alpha_P;
+        r.alpha_pi = p->alpha_pi;
+        r.p_mean_lo = p->p_mean_lo;
+        r.p_mean_hi = p->p_mean_hi;
+        r.p_var = p->p_var;
+        for (int i = 0; i < 4; ++i) r.box[i] = p->box[i];
+        r.iw_df = p->iw_df;
+    } else {
+        r.alpha_P = 0.01;
+        r.alpha_pi = 1.0;
+        r.p_mean_lo = 0.1;
+        r.p_mean_hi = 0.9;
+        r.p_var = 0.001;
+        r.box[0] = 0;
+        r.box[1] = 300;
+        r.box[2] = 0;
+        r.box[3] = 150;
+        r.iw_df = K;
+    }
+    return r;
+}
+
+static size_t smem_for(int D) { return sizeof(double) * ((size_t)D + TPB); }
+
+extern "C" {
+
+int32_t hmm_theta_dim(int32_t K) { return K * K + 6 * K - 1; }
+
+void hmm_prior_default(hmm_prior *p, int32_t K) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->alpha_P = 0.01f;
+    p->alpha_pi = 1.0f;
+    p->p_mean_lo = 0.1f;
+    p->p_mean_hi = 0.9f;
+    p->p_var = 0.001f;
+    p->box[0] = 0.f;
+    p->box[1] = 300.f;
+    p->box[2] = 0.f;
+    p->box[3] = 150.f;
+    p->iw_df = (float)K;
+}
+
+int hmm_theta_to_params(int32_t n, int32_t K, const float *theta, const hmm_prior *prior, float *pi, float *P,
+                        float *p_tremor, float *mu, float *cov, double *logprior, void *stream) {
+    if (n < 1 || K < 2 || K > 80 || !theta || !pi || !P || !p_tremor || !mu || !cov || !logprior)
+        return HMM_EINVAL;
+    const int D = hmm_theta_dim(K);
+    const Prior pr = to_prior(prior, K);
+    transform_kernel<<<n, TPB, smem_for(D), (cudaStream_t)stream>>>(K, D, theta, pr, pi, P, p_tremor, mu, cov,
+                                                                     logprior);
+    return cudaGetLastError() == cudaSuccess ? HMM_OK : HMM_ECUDA;
+}
+
+int hmm_sampler_destroy(hmm_sampler *s) {
+    if (!s) return HMM_OK;
+    if (s->own) cudaStreamSynchronize(s->own);
+    if (s->exec) cudaGraphExecDestroy(s->exec);
+    if (s->graph) cudaGraphDestroy(s->graph);
+    if (s->ev_in) cudaEventDestroy(s->ev_in);
+    if (s->ev_out) cudaEventDestroy(s->ev_out);
+    if (s->own) cudaStreamDestroy(s->own);
+    void *bufs[] = {s->theta, s->theta_prop, s->step, s->pi, s->P, s->p, s->mu, s->cov, s->logpost, s->loglik,
+                    s->logprior, s->loglik_prop, s->logprior_prop, s->n_acc, s->ctl, s->loglik32,
+                    s->recheck_maxdiff};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    delete[] s->offs;
+    if (s->lik) hmm_destroy(s->lik);
+    if (s->lik32) hmm_destroy(s->lik32);
+    delete s;
+    return HMM_OK;
+}
+
+int hmm_sampler_create(hmm_sampler **out, int device, int32_t n_chains, int32_t K, const hmm_prior *prior,
+                       const float *theta0, const float *step, uint64_t seed, int32_t n_seg,
+                       const int64_t *seg_offsets, const float *xy, const uint8_t *tremor, const hmm_opts *opts,
+                       void *stream) {
+    if (!out) return HMM_EINVAL;
+    *out = nullptr;
+    if (n_chains < 1 || K < 2 || K > 80 || !theta0 || !step || n_seg < 1 || !seg_offsets) return HMM_EINVAL;
+    hmm_sampler *s = new (std::nothrow) hmm_sampler();
+    if (!s) return HMM_ENOMEM;
+    int rc = hmm_create(&s->lik, device);
+    if (rc) {
+        delete s;
+        return rc;
+    }
+    const int C = n_chains, D = hmm_theta_dim(K);
+    s->C = C;
+    s->K = K;
+    s->D = D;
+    s->seed = seed;
+    s->prior = to_prior(prior, K);
+    if (opts) s->opts = *opts; else hmm_opts_default(&s->opts);
+    s->n_seg = n_seg;
+    s->offs = new int64_t[n_seg + 1];
+    memcpy(s->offs, seg_offsets, sizeof(int64_t) * (n_seg + 1));
+    s->xy = xy;
+    s->tremor = tremor;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void **p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    };
+    alloc((void **)&s->theta, sizeof(float) * C * D);
+    alloc((void **)&s->theta_prop, sizeof(float) * C * D);
+    alloc((void **)&s->step, sizeof(float) * D);
+    alloc((void **)&s->pi, sizeof(float) * C * K);
+    alloc((void **)&s->P, sizeof(float) * C * K * K);
+    alloc((void **)&s->p, sizeof(float) * C * K);
+    alloc((void **)&s->mu, sizeof(float) * C * 2 * K);
+    alloc((void **)&s->cov, sizeof(float) * C * 3 * K);
+    alloc((void **)&s->logpost, sizeof(double) * C);
+    alloc((void **)&s->loglik, sizeof(double) * C);
+    alloc((void **)&s->logprior, sizeof(double) * C);
+    alloc((void **)&s->loglik_prop, sizeof(double) * C);
+    alloc((void **)&s->logprior_prop, sizeof(double) * C);
+    alloc((void **)&s->n_acc, sizeof(unsigned long long) * C);
+    alloc((void **)&s->ctl, sizeof(Ctl));
+    alloc((void **)&s->loglik32, sizeof(double) * C);
+    alloc((void **)&s->recheck_maxdiff, sizeof(double));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        hmm_sampler_destroy(s);
+        return HMM_ENOMEM;
+    }
+    Ctl c0{};
+    e = cudaMemcpyAsync(s->theta, theta0, sizeof(float) * C * D, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->step, step, sizeof(float) * D, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->n_acc, 0, sizeof(unsigned long long) * C, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->ctl, &c0, sizeof(Ctl), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        hmm_sampler_destroy(s);
+        return HMM_ECUDA;
+    }
+    // initial state: parameters, log prior, log likelihood, log posterior
+    transform_kernel<<<C, TPB, smem_for(D), st>>>(K, D, s->theta, s->prior, s->pi, s->P, s->p, s->mu, s->cov,
+                                                   s->logprior);
+    rc = hmm_loglik_batched(s->lik, C, K, s->pi, s->P, s->p, s->mu, s->cov, n_seg, s->offs, xy, tremor, &s->opts,
+                            s->loglik, stream);
+    if (rc == HMM_OK) {
+        sum_kernel<<<(C + 127) / 128, 128, 0, st>>>(C, s->loglik, s->logprior, s->logpost);
+        if (cudaGetLastError() != cudaSuccess) rc = HMM_ECUDA;
+    }
+    if (rc != HMM_OK) {
+        hmm_sampler_destroy(s);
+        return rc;
+    }
+    *out = s;
+    return HMM_OK;
+}
+
+static int recheck(hmm_sampler *s, cudaStream_t st);
+
+// one iteration's launches (also what the graph captures)
+static int iteration(hmm_sampler *s, cudaStream_t st) {
+    const int C = s->C, K = s->K, D = s->D;
+    propose_kernel<<<C, TPB, smem_for(D), st>>>(K, D, s->theta, s->step, s->seed, s->ctl, s->prior, s->theta_prop,
+                                                 s->pi, s->P, s->p, s->mu, s->cov, s->logprior_prop);
+    if (cudaGetLastError() != cudaSuccess) return HMM_ECUDA;
+    int rc = hmm_loglik_batched(s->lik, C, K, s->pi, s->P, s->p, s->mu, s->cov, s->n_seg, s->offs, s->xy,
+                                s->tremor, &s->opts, s->loglik_prop, st);
+    if (rc) return rc;
+    s->launches_per_iter = hmm_last_launch_count(s->lik) + 3;
+    accept_kernel<<<C, TPB, 0, st>>>(D, s->seed, s->ctl, s->theta, s->theta_prop, s->logpost, s->loglik,
+                                     s->logprior, s->loglik_prop, s->logprior_prop, nullptr, s->n_acc);
+    advance_kernel<<<1, 1, 0, st>>>(s->ctl);
+    return cudaGetLastError() == cudaSuccess ? HMM_OK : HMM_ECUDA;
+}
+
+static int mcmc_step_own(hmm_sampler *s, int32_t n_iter, float *trace_logpost, float *trace_theta,
+                         cudaStream_t st);
+
+int hmm_mcmc_step(hmm_sampler *s, int32_t n_iter, float *trace_logpost, float *trace_theta, void *stream) {
+    if (!s || n_iter < 0) return HMM_EINVAL;
+    if (n_iter == 0) return HMM_OK;
+    cudaStream_t user = (cudaStream_t)stream;
+    if (cudaEventRecord(s->ev_in, user) != cudaSuccess || cudaStreamWaitEvent(s->own, s->ev_in, 0) != cudaSuccess)
+        return HMM_ECUDA;
+    const int rc = mcmc_step_own(s, n_iter, trace_logpost, trace_theta, s->own);
+    if (cudaEventRecord(s->ev_out, s->own) != cudaSuccess || cudaStreamWaitEvent(user, s->ev_out, 0) != cudaSuccess)
+        return rc ? rc : HMM_ECUDA;
+    return rc;
+}
+
+static int mcmc_step_own(hmm_sampler *s, int32_t n_iter, float *trace_logpost, float *trace_theta,
+                         cudaStream_t st) {
+    // per-call control block: trace destinations and the first iteration index
+    Ctl c{};
+    c.iter = s->iter_host;
+    c.iter0 = s->iter_host;
+    c.trace_lp = trace_logpost;
+    c.trace_theta = trace_theta;
+    cudaError_t e = cudaMemcpyAsync(s->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // &c is a stack object
+    if (e != cudaSuccess) return HMM_ECUDA;
+    int done = 0;
+    if (!s->exec && s->graph_failed) {
+        for (; done < n_iter; ++done) {
+            int rc = iteration(s, st);
+            if (rc) return rc;
+        }
+        s->iter_host += n_iter;
+        if (s->opts.recheck_fp32 && s->opts.precision != HMM_PREC_FP32_SIMT) return recheck(s, st);
+        return HMM_OK;
+    }
+    if (!s->exec) {
+        // first iteration runs directly (sizes the workspace, uploads the plan),
+        // the second is captured once and replayed from then on
+        int rc = iteration(s, st);
+        if (rc) return rc;
+        ++done;
+        if (done < n_iter) {
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+            if (e == cudaSuccess) {
+                rc = iteration(s, st);
+                e = cudaStreamEndCapture(st, &g);
+                if (rc == HMM_OK && e == cudaSuccess) e = cudaGraphInstantiate(&s->exec, g, 0);
+                if (e == cudaSuccess) s->graph = g; else if (g) cudaGraphDestroy(g);
+            }
+            if (e != cudaSuccess || rc != HMM_OK) {
+                cudaGetLastError();
+                if (s->exec) {
+                    cudaGraphExecDestroy(s->exec);
+                    s->exec = nullptr;
+                }
+                // fall back to direct launches for the rest of this call
+                s->graph_failed = 1;
+                for (; done < n_iter; ++done) {
+                    rc = iteration(s, st);
+                    if (rc) return rc;
+                }
+                s->iter_host += n_iter;
+                if (s->opts.recheck_fp32 && s->opts.precision != HMM_PREC_FP32_SIMT) return recheck(s, st);
+                return HMM_OK;
+            }
+        }
+    }
+    for (; done < n_iter; ++done) {
+        e = cudaGraphLaunch(s->exec, st);
+        if (e != cudaSuccess) return HMM_ECUDA;
+    }
+    s->iter_host += n_iter;
+    if (s->opts.recheck_fp32 && s->opts.precision != HMM_PREC_FP32_SIMT) return recheck(s, st);
+    return HMM_OK;
+}
+
+// FP32-SIMT re-evaluation of every chain's current state (precision rows of
+// the batched path: the reported log likelihood becomes the FP32 one)
+static int recheck(hmm_sampler *s, cudaStream_t st) {
+    if (!s->lik32) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        int rc = hmm_create(&s->lik32, dev);
+        if (rc) return rc;
+    }
+    const int C = s->C, K = s->K, D = s->D;
+    transform_kernel<<<C, TPB, smem_for(D), st>>>(K, D, s->theta, s->prior, s->pi, s->P, s->p, s->mu, s->cov,
+                                                   s->logprior_prop);
+    hmm_opts o = s->opts;
+    o.precision = HMM_PREC_FP32_SIMT;
+    o.chunk_len = 0;
+    o.recheck_fp32 = 0;
+    int rc = hmm_loglik_batched(s->lik32, C, K, s->pi, s->P, s->p, s->mu, s->cov, s->n_seg, s->offs, s->xy,
+                                s->tremor, &o, s->loglik32, st);
+    if (rc) return rc;
+    recheck_kernel<<<1, 128, 0, st>>>(C, s->loglik32, s->loglik, s->logpost, s->logprior, s->recheck_maxdiff);
+    return cudaGetLastError() == cudaSuccess ? HMM_OK : HMM_ECUDA;
+}
+
+int hmm_sampler_recheck(hmm_sampler *s, double *max_abs_change_dev, void *stream) {
+    if (!s) return HMM_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = recheck(s, st);
+    if (rc) return rc;
+    if (max_abs_change_dev &&
+        cudaMemcpyAsync(max_abs_change_dev, s->recheck_maxdiff, sizeof(double), cudaMemcpyDeviceToDevice, st) !=
+            cudaSuccess)
+        return HMM_ECUDA;
+    return HMM_OK;
+}
+
+int hmm_sampler_state(hmm_sampler *s, float *theta_out, double *logpost_out, double *loglik_out,
+                      unsigned long long *n_accept_out, void *stream) {
+    if (!s) return HMM_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (theta_out) e = cudaMemcpyAsync(theta_out, s->theta, sizeof(float) * s->C * s->D, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && logpost_out)
+        e = cudaMemcpyAsync(logpost_out, s->logpost, sizeof(double) * s->C, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && loglik_out)
+        e = cudaMemcpyAsync(loglik_out, s->loglik, sizeof(double) * s->C, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && n_accept_out)
+        e = cudaMemcpyAsync(n_accept_out, s->n_acc, sizeof(unsigned long long) * s->C, cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? HMM_OK : HMM_ECUDA;
+}
+
+int hmm_sampler_launches_per_iter(const hmm_sampler *s) { return s ? s->launches_per_iter : -1; }
+
+int hmm_sampler_graph_active(const hmm_sampler *s) { return s ? (s->exec != nullptr ? 1 : 0) : -1; }
+
+}  // extern "C"
