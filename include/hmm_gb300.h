@@ -273,6 +273,82 @@ int hmm_sampler_launches_per_iter(const hmm_sampler *sampler);
  * directly (before the second iteration, or if capture failed). */
 int hmm_sampler_graph_active(const hmm_sampler *sampler);
 
+/* ---- learned proposal (a small MLP trained on the random walk's history) ---- */
+
+#define HMM_PROPOSAL_RW 0   /* theta' = theta + step * N(0, I)                        */
+#define HMM_PROPOSAL_MLP 1  /* theta' ~ q(. | theta) given by an hmm_mlp (see below)   */
+
+typedef struct hmm_mlp hmm_mlp;
+
+/*
+ * The network: x = (theta - mean) / in_scale (d inputs) -> relu(W1 x + b1)
+ * (hidden) -> relu(W2 h1 + b2) (hidden) -> W3 h2 + b3 = (f_mu, f_sig) (2d).
+ * The proposal it defines is
+ *   q(theta' | theta) = N(theta + lam scale gamma f_mu, diag((lam scale exp(f_sig))^2)),
+ * f_sig clamped to [-6, 3]; Metropolis-Hastings adds the correction
+ * log q(theta | theta') - log q(theta' | theta), so the chain's target (the
+ * posterior of Section "Monte Carlo Markov Chains") is unchanged.
+ * Parameters live on the device, FP32, flattened as W1 [hidden][d], b1,
+ * W2 [hidden][hidden], b2, W3 [2d][hidden], b3. Created with He-uniform
+ * weights (Philox, `seed`), zero biases, a small last layer, mean 0,
+ * in_scale 1, scale 1.
+ */
+int hmm_mlp_create(hmm_mlp **mlp, int32_t d, int32_t hidden, uint64_t seed, void *stream);
+int hmm_mlp_destroy(hmm_mlp *mlp);
+int64_t hmm_mlp_num_params(const hmm_mlp *mlp);
+
+/* Copy the flattened parameters to (set = 0) or from (set = 1) params_dev. */
+int hmm_mlp_params(hmm_mlp *mlp, float *params_dev, int set, void *stream);
+
+/* Input standardisation (device mean[d], in_scale[d]), proposal scale (device
+ * scale[d]) and the global step factor lam > 0. */
+int hmm_mlp_set_scaling(hmm_mlp *mlp, const float *mean_dev, const float *in_scale_dev, const float *scale_dev,
+                        float lam, void *stream);
+
+/* Raw outputs (f_mu, f_sig) for B states: theta [B][d] -> out [B][2d] (device). */
+int hmm_mlp_forward(hmm_mlp *mlp, int32_t B, const float *theta, float *out_dev, void *stream);
+
+/*
+ * Training loss on B pairs (theta_b, y_b), y being a later state of the same
+ * chain: loss = mean_b sum_i ((y - theta)_i / scale_i - f_mu,i)^2 /
+ * (2 exp(2 f_sig,i)) + f_sig,i (the negative log density of y under q with
+ * lam = 1, without constants). Writes the loss (device double) and keeps the
+ * gradient wrt every parameter; grads_dev (device, num_params floats) may be
+ * NULL or receives a copy.
+ */
+int hmm_mlp_loss_grad(hmm_mlp *mlp, int32_t B, const float *theta, const float *y, double *loss_dev,
+                      float *grads_dev, void *stream);
+
+/* One Adam step (bias-corrected) with the gradient of the last hmm_mlp_loss_grad. */
+int hmm_mlp_adam_step(hmm_mlp *mlp, float lr, float beta1, float beta2, float eps, void *stream);
+
+/*
+ * Set the scalings from n training pairs (X[n][d], Y[n][d], device): mean and
+ * in_scale = column means and standard deviations of X, scale = column
+ * standard deviations of Y - X; and the proposal's step factor lam.
+ */
+int hmm_mlp_fit_scaling(hmm_mlp *mlp, int32_t n, const float *X, const float *Y, float lam, void *stream);
+
+/* Change the step factor lam > 0 and the drift factor gamma >= 0 (created: 1, 1). */
+int hmm_mlp_set_lambda(hmm_mlp *mlp, float lam, float gamma);
+
+/*
+ * n_steps Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr),
+ * each on `batch` pairs drawn with replacement (Philox, `seed`) from X/Y
+ * (device [n][d]). loss_trace (device double [n_steps], may be NULL) gets
+ * each step's minibatch loss. Synchronises `stream` before returning.
+ */
+int hmm_mlp_train(hmm_mlp *mlp, int32_t n, const float *X, const float *Y, int32_t n_steps, int32_t batch,
+                  float lr, uint64_t seed, double *loss_trace, void *stream);
+
+/*
+ * Switch a sampler's proposal (HMM_PROPOSAL_RW or HMM_PROPOSAL_MLP with an
+ * mlp whose d is the sampler's theta dimension; the sampler reads the
+ * network at every iteration, so keep it alive and do not train it while the
+ * sampler runs). The next hmm_mcmc_step captures a new graph.
+ */
+int hmm_sampler_set_proposal(hmm_sampler *sampler, int32_t kind, hmm_mlp *mlp);
+
 /* ---- allocation-free variant ---- */
 #define HMM_NOALLOC_MAX_K 32             /* largest state count it accepts  */
 #define HMM_NOALLOC_MAX_T (1LL << 20)    /* longest sequence it accepts     */

@@ -18,7 +18,7 @@ from pathlib import Path
 import numpy as np
 
 _HERE = Path(__file__).resolve().parent
-_SRC = [_HERE / "hmm_oracle.c", _HERE / "mcmc_oracle.c"]
+_SRC = [_HERE / "hmm_oracle.c", _HERE / "mcmc_oracle.c", _HERE / "mlp_oracle.c"]
 _BUILD = _HERE / "_build"
 _lib = None
 
@@ -100,6 +100,14 @@ def _declare_mcmc(L):
     L.oracle_theta_dim.restype = ctypes.c_int
     L.oracle_theta_to_params.argtypes = [ctypes.c_int, _d, ctypes.POINTER(OraclePrior), _d, _d, _d, _d, _d]
     L.oracle_theta_to_params.restype = ctypes.c_double
+    if hasattr(L, "oracle_mlp_forward"):
+        L.oracle_mlp_forward.argtypes = [ctypes.c_int, ctypes.c_int, _d, _d, _d, ctypes.c_int, _d, _d]
+        L.oracle_mlp_forward.restype = None
+        L.oracle_mlp_loss_grad.argtypes = [ctypes.c_int, ctypes.c_int, _d, _d, _d, _d, ctypes.c_int, _d, _d, _d]
+        L.oracle_mlp_loss_grad.restype = ctypes.c_double
+        L.oracle_adam_step.argtypes = [ctypes.c_size_t, _d, _d, _d, _d, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.oracle_adam_step.restype = None
 
 
 def default_prior(K, box=(0.0, 300.0, 0.0, 150.0)):
@@ -227,3 +235,39 @@ def loglik_batched(prm, xy, tremor, offsets, init_mode: int = 0, n_threads: int 
                                 tremor.ctypes.data_as(_u8), int(init_mode),
                                 out.ctypes.data_as(_d), int(n_threads))
     return out
+
+
+def _dp(a):
+    return a.ctypes.data_as(_d)
+
+
+def _c64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def mlp_num_params(d, H):
+    return H * d + H + H * H + H + 2 * d * H + 2 * d
+
+
+def mlp_forward(params, d, H, mean, in_scale, theta):
+    p, m, s, th = _c64(params), _c64(mean), _c64(in_scale), _c64(theta).reshape(-1, d)
+    out = np.zeros((th.shape[0], 2 * d))
+    lib().oracle_mlp_forward(d, H, _dp(p), _dp(m), _dp(s), th.shape[0], _dp(th), _dp(out))
+    return out
+
+
+def mlp_loss_grad(params, d, H, mean, in_scale, scale, theta, y):
+    p, m, si, s = _c64(params), _c64(mean), _c64(in_scale), _c64(scale)
+    th, yy = _c64(theta).reshape(-1, d), _c64(y).reshape(-1, d)
+    g = np.zeros(mlp_num_params(d, H))
+    loss = lib().oracle_mlp_loss_grad(d, H, _dp(p), _dp(m), _dp(si), _dp(s), th.shape[0], _dp(th), _dp(yy),
+                                      _dp(g))
+    return loss, g
+
+
+def adam_step(params, grad, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """In-place Adam step on float64 arrays (returns them)."""
+    for a in (params, grad, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    lib().oracle_adam_step(params.size, _dp(params), _dp(grad), _dp(m), _dp(v), int(t), lr, b1, b2, eps)
+    return params, m, v

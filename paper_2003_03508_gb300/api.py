@@ -32,6 +32,9 @@ HMM_PREC_TF32_SPLIT = 3
 HMM_INIT_EMIT_FIRST = 0
 HMM_INIT_TRANSITION_FIRST = 1
 
+HMM_PROPOSAL_RW = 0
+HMM_PROPOSAL_MLP = 1
+
 PRECISIONS = {"fp32": HMM_PREC_FP32_SIMT, "tf32": HMM_PREC_TF32, "bf16": HMM_PREC_BF16,
               "tf32_split": HMM_PREC_TF32_SPLIT}
 
@@ -99,6 +102,18 @@ SIGNATURES = {
     "hmm_sampler_state": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "hmm_sampler_launches_per_iter": (ctypes.c_int, [_VP]),
     "hmm_sampler_graph_active": (ctypes.c_int, [_VP]),
+    "hmm_mlp_create": (ctypes.c_int, [ctypes.POINTER(_VP), _I32, _I32, ctypes.c_uint64, _VP]),
+    "hmm_mlp_destroy": (ctypes.c_int, [_VP]),
+    "hmm_mlp_num_params": (ctypes.c_int64, [_VP]),
+    "hmm_mlp_params": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP]),
+    "hmm_mlp_set_scaling": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_float, _VP]),
+    "hmm_mlp_forward": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP]),
+    "hmm_mlp_loss_grad": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP, _VP, _VP]),
+    "hmm_mlp_adam_step": (ctypes.c_int, [_VP, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _VP]),
+    "hmm_mlp_fit_scaling": (ctypes.c_int, [_VP, _I32, _VP, _VP, ctypes.c_float, _VP]),
+    "hmm_mlp_set_lambda": (ctypes.c_int, [_VP, ctypes.c_float, ctypes.c_float]),
+    "hmm_mlp_train": (ctypes.c_int, [_VP, _I32, _VP, _VP, _I32, _I32, ctypes.c_float, ctypes.c_uint64, _VP, _VP]),
+    "hmm_sampler_set_proposal": (ctypes.c_int, [_VP, _I32, _VP]),
     "hmm_loglik_noalloc": (ctypes.c_int, [ctypes.POINTER(hmm_params), ctypes.POINTER(hmm_obs), _VP, _VP]),
     "hmm_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "hmm_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
@@ -405,6 +420,97 @@ class Sampler:
     @property
     def graph_active(self):
         return bool(self.lib.hmm_sampler_graph_active(self.h))
+
+    def set_proposal(self, mlp=None):
+        """Use the learned proposal of `mlp` (an MLP), or the random walk (None)."""
+        kind = HMM_PROPOSAL_MLP if mlp is not None else HMM_PROPOSAL_RW
+        rc = self.lib.hmm_sampler_set_proposal(self.h, kind, mlp.h if mlp is not None else None)
+        if rc != HMM_OK:
+            raise HMMError(rc, "hmm_sampler_set_proposal failed")
+        self._mlp = mlp
+
+
+class MLP:
+    """The learned proposal's network (wraps hmm_mlp)."""
+
+    def __init__(self, d, hidden=256, seed=0, stream=None):
+        self.lib = load_library()
+        self.d, self.hidden = int(d), int(hidden)
+        h = _VP()
+        rc = self.lib.hmm_mlp_create(ctypes.byref(h), self.d, self.hidden, int(seed), _stream_ptr(stream))
+        if rc != HMM_OK:
+            raise HMMError(rc, "hmm_mlp_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hmm_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ok(self, rc, what):
+        if rc != HMM_OK:
+            raise HMMError(rc, what)
+
+    @property
+    def num_params(self):
+        return int(self.lib.hmm_mlp_num_params(self.h))
+
+    def get_params(self, stream=None):
+        out = torch.empty(self.num_params, device="cuda")
+        self._ok(self.lib.hmm_mlp_params(self.h, out.data_ptr(), 0, _stream_ptr(stream)), "get params")
+        return out
+
+    def set_params(self, p, stream=None):
+        _dev(p, torch.float32, "params")
+        self._ok(self.lib.hmm_mlp_params(self.h, p.data_ptr(), 1, _stream_ptr(stream)), "set params")
+
+    def set_scaling(self, mean, in_scale, scale, lam, stream=None):
+        _dev(mean, torch.float32, "mean"); _dev(in_scale, torch.float32, "in_scale")
+        _dev(scale, torch.float32, "scale")
+        self._ok(self.lib.hmm_mlp_set_scaling(self.h, mean.data_ptr(), in_scale.data_ptr(), scale.data_ptr(),
+                                              float(lam), _stream_ptr(stream)), "set scaling")
+
+    def fit_scaling(self, X, Y, lam, stream=None):
+        _dev(X, torch.float32, "X"); _dev(Y, torch.float32, "Y")
+        self._ok(self.lib.hmm_mlp_fit_scaling(self.h, int(X.shape[0]), X.data_ptr(), Y.data_ptr(), float(lam),
+                                              _stream_ptr(stream)), "fit scaling")
+
+    def set_lambda(self, lam, gamma=1.0):
+        self._ok(self.lib.hmm_mlp_set_lambda(self.h, float(lam), float(gamma)), "set lambda")
+
+    def forward(self, theta, stream=None):
+        _dev(theta, torch.float32, "theta")
+        out = torch.empty(theta.shape[0], 2 * self.d, device="cuda")
+        self._ok(self.lib.hmm_mlp_forward(self.h, int(theta.shape[0]), theta.data_ptr(), out.data_ptr(),
+                                          _stream_ptr(stream)), "forward")
+        return out
+
+    def loss_grad(self, theta, y, stream=None):
+        _dev(theta, torch.float32, "theta"); _dev(y, torch.float32, "y")
+        loss = torch.empty(1, dtype=torch.float64, device="cuda")
+        g = torch.empty(self.num_params, device="cuda")
+        self._ok(self.lib.hmm_mlp_loss_grad(self.h, int(theta.shape[0]), theta.data_ptr(), y.data_ptr(),
+                                            loss.data_ptr(), g.data_ptr(), _stream_ptr(stream)), "loss/grad")
+        return loss, g
+
+    def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        self._ok(self.lib.hmm_mlp_adam_step(self.h, float(lr), float(beta1), float(beta2), float(eps),
+                                            _stream_ptr(stream)), "adam")
+
+    def train(self, X, Y, n_steps, batch=256, lr=1e-3, seed=0, stream=None):
+        """n_steps Adam steps on minibatches of (X, Y) pairs; returns the loss trace (CUDA float64)."""
+        _dev(X, torch.float32, "X"); _dev(Y, torch.float32, "Y")
+        tr = torch.empty(max(1, n_steps), dtype=torch.float64, device="cuda")
+        self._ok(self.lib.hmm_mlp_train(self.h, int(X.shape[0]), X.data_ptr(), Y.data_ptr(), int(n_steps),
+                                        int(batch), float(lr), int(seed), tr.data_ptr(), _stream_ptr(stream)),
+                 "train")
+        return tr[:n_steps]
 
 
 _default_ctx = {}

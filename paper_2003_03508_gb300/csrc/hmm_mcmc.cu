@@ -28,7 +28,15 @@
 
 #include "hmm_internal.cuh"
 
+struct hmm_mlp;
 namespace hmm {
+int mlp_dim(const hmm_mlp *m);
+int mlp_hidden(const hmm_mlp *m);
+float mlp_lambda(const hmm_mlp *m);
+float mlp_drift(const hmm_mlp *m);
+const float *mlp_scale(const hmm_mlp *m);
+int mlp_eval(hmm_mlp *m, int B, const float *theta, float *x, float *a1, float *a2, float *out, cudaStream_t st);
+
 namespace mcmc {
 
 constexpr uint32_t PH_M0 = 0xD2511F53u, PH_M1 = 0xCD9E8D57u, PH_W0 = 0x9E3779B9u, PH_W1 = 0xBB67AE85u;
@@ -191,6 +199,64 @@ __global__ void __launch_bounds__(TPB) propose_kernel(int K, int D, const float 
     if (threadIdx.x == 0) logprior[c] = lp;
 }
 
+constexpr float FSIG_LO = -6.0f, FSIG_HI = 3.0f;  // same clamp as the network's training loss
+
+// learned proposal: theta' = theta + lam s (gamma f_mu + exp(f_sig) z), z ~ N(0, I)
+// (Philox); logq[c] = log q(theta' | theta) up to terms that cancel in the
+// ratio; then theta' -> parameters + log density
+__global__ void __launch_bounds__(TPB) propose_mlp_kernel(int K, int D, const float *__restrict__ theta,
+                                                          const float *__restrict__ net, const float *__restrict__ scale,
+                                                          float lam, float gam, uint64_t seed, const Ctl *__restrict__ ctl, Prior pr,
+                                                          float *theta_prop, double *logq, float *pi, float *P,
+                                                          float *p, float *mu, float *cov, double *logprior) {
+    extern __shared__ double sm[];
+    double *th = sm;
+    double *red = sm + D;
+    const int c = blockIdx.x;
+    const uint32_t it = (uint32_t)ctl->iter;
+    double lq = 0.0;
+    for (int d = threadIdx.x; d < D; d += TPB) {
+        const double z = normal_draw(seed, (uint32_t)c, it, (uint32_t)d);
+        const float fmu = gam * net[(size_t)c * 2 * D + d];
+        const float fs = fminf(fmaxf(net[(size_t)c * 2 * D + D + d], FSIG_LO), FSIG_HI);
+        const double sd = (double)lam * scale[d] * exp((double)fs);
+        const float v = (float)((double)theta[(size_t)c * D + d] + (double)lam * scale[d] * fmu + sd * z);
+        theta_prop[(size_t)c * D + d] = v;
+        th[d] = v;
+        // density of the rounded proposal under q (standardised residual)
+        const double r = ((double)v - theta[(size_t)c * D + d] - (double)lam * scale[d] * fmu) / sd;
+        lq += -0.5 * r * r - log(sd);
+    }
+    const double lqs = block_sum(lq, red);
+    if (threadIdx.x == 0) logq[c] = lqs;
+    __syncthreads();
+    const double lp = transform(K, th, pr, pi + (size_t)c * K, P + (size_t)c * K * K, p + (size_t)c * K,
+                                mu + (size_t)c * 2 * K, cov + (size_t)c * 3 * K, red);
+    if (threadIdx.x == 0) logprior[c] = lp;
+}
+
+// qcorr[c] = log q(theta | theta') - log q(theta' | theta), with the network
+// evaluated at theta' (net_rev)
+__global__ void __launch_bounds__(TPB) qcorr_kernel(int D, const float *__restrict__ theta,
+                                                    const float *__restrict__ theta_prop,
+                                                    const float *__restrict__ net_rev, const float *__restrict__ scale,
+                                                    float lam, float gam, const double *__restrict__ logq_fwd,
+                                                    double *qcorr) {
+    __shared__ double red[TPB];
+    const int c = blockIdx.x;
+    double lq = 0.0;
+    for (int d = threadIdx.x; d < D; d += TPB) {
+        const float fmu = gam * net_rev[(size_t)c * 2 * D + d];
+        const float fs = fminf(fmaxf(net_rev[(size_t)c * 2 * D + D + d], FSIG_LO), FSIG_HI);
+        const double sd = (double)lam * scale[d] * exp((double)fs);
+        const double r = ((double)theta[(size_t)c * D + d] - theta_prop[(size_t)c * D + d] -
+                          (double)lam * scale[d] * fmu) / sd;
+        lq += -0.5 * r * r - log(sd);
+    }
+    const double s = block_sum(lq, red);
+    if (threadIdx.x == 0) qcorr[c] = s - logq_fwd[c];
+}
+
 // Metropolis-Hastings decision: accept when log u < (log L' + log pi') -
 // (log L + log pi) + qcorr (qcorr = log q(theta|theta') - log q(theta'|theta),
 // zero for the symmetric random walk).
@@ -286,6 +352,11 @@ struct hmm_sampler {
     cudaGraphExec_t exec = nullptr;
     int launches_per_iter = 0;
     int graph_failed = 0;
+    // learned proposal (HMM_PROPOSAL_MLP): network and its buffers
+    int kind = HMM_PROPOSAL_RW;
+    hmm_mlp *mlp = nullptr;
+    float *mx = nullptr, *ma1 = nullptr, *ma2 = nullptr, *net_f = nullptr, *net_r = nullptr;
+    double *logq = nullptr, *qcorr = nullptr;
     // iterations run on the sampler's own stream (the legacy default stream
     // cannot be captured), ordered against the caller's stream by events
     cudaStream_t own = nullptr;
@@ -359,7 +430,7 @@ int hmm_sampler_destroy(hmm_sampler *s) {
     if (s->own) cudaStreamDestroy(s->own);
     void *bufs[] = {s->theta, s->theta_prop, s->step, s->pi, s->P, s->p, s->mu, s->cov, s->logpost, s->loglik,
                     s->logprior, s->loglik_prop, s->logprior_prop, s->n_acc, s->ctl, s->loglik32,
-                    s->recheck_maxdiff};
+                    s->recheck_maxdiff, s->mx, s->ma1, s->ma2, s->net_f, s->net_r, s->logq, s->qcorr};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete[] s->offs;
@@ -458,15 +529,31 @@ static int recheck(hmm_sampler *s, cudaStream_t st);
 // one iteration's launches (also what the graph captures)
 static int iteration(hmm_sampler *s, cudaStream_t st) {
     const int C = s->C, K = s->K, D = s->D;
-    propose_kernel<<<C, TPB, smem_for(D), st>>>(K, D, s->theta, s->step, s->seed, s->ctl, s->prior, s->theta_prop,
-                                                 s->pi, s->P, s->p, s->mu, s->cov, s->logprior_prop);
+    int extra = 0;
+    if (s->kind == HMM_PROPOSAL_MLP) {
+        const float lam = mlp_lambda(s->mlp);
+        const float *scale = mlp_scale(s->mlp);
+        if (mlp_eval(s->mlp, C, s->theta, s->mx, s->ma1, s->ma2, s->net_f, st)) return HMM_ECUDA;
+        const float gam = mlp_drift(s->mlp);
+        propose_mlp_kernel<<<C, TPB, smem_for(D), st>>>(K, D, s->theta, s->net_f, scale, lam, gam, s->seed, s->ctl,
+                                                         s->prior, s->theta_prop, s->logq, s->pi, s->P, s->p, s->mu,
+                                                         s->cov, s->logprior_prop);
+        if (mlp_eval(s->mlp, C, s->theta_prop, s->mx, s->ma1, s->ma2, s->net_r, st)) return HMM_ECUDA;
+        qcorr_kernel<<<C, TPB, 0, st>>>(D, s->theta, s->theta_prop, s->net_r, scale, lam, gam, s->logq, s->qcorr);
+        extra = 2 * 4 + 1;  // two network evaluations (standardise + 3 GEMMs) and the q ratio
+    } else {
+        propose_kernel<<<C, TPB, smem_for(D), st>>>(K, D, s->theta, s->step, s->seed, s->ctl, s->prior,
+                                                     s->theta_prop, s->pi, s->P, s->p, s->mu, s->cov,
+                                                     s->logprior_prop);
+    }
     if (cudaGetLastError() != cudaSuccess) return HMM_ECUDA;
     int rc = hmm_loglik_batched(s->lik, C, K, s->pi, s->P, s->p, s->mu, s->cov, s->n_seg, s->offs, s->xy,
                                 s->tremor, &s->opts, s->loglik_prop, st);
     if (rc) return rc;
-    s->launches_per_iter = hmm_last_launch_count(s->lik) + 3;
+    s->launches_per_iter = hmm_last_launch_count(s->lik) + 3 + extra;
     accept_kernel<<<C, TPB, 0, st>>>(D, s->seed, s->ctl, s->theta, s->theta_prop, s->logpost, s->loglik,
-                                     s->logprior, s->loglik_prop, s->logprior_prop, nullptr, s->n_acc);
+                                     s->logprior, s->loglik_prop, s->logprior_prop,
+                                     s->kind == HMM_PROPOSAL_MLP ? s->qcorr : nullptr, s->n_acc);
     advance_kernel<<<1, 1, 0, st>>>(s->ctl);
     return cudaGetLastError() == cudaSuccess ? HMM_OK : HMM_ECUDA;
 }
@@ -597,6 +684,44 @@ int hmm_sampler_state(hmm_sampler *s, float *theta_out, double *logpost_out, dou
     if (e == cudaSuccess && n_accept_out)
         e = cudaMemcpyAsync(n_accept_out, s->n_acc, sizeof(unsigned long long) * s->C, cudaMemcpyDeviceToDevice, st);
     return e == cudaSuccess ? HMM_OK : HMM_ECUDA;
+}
+
+int hmm_sampler_set_proposal(hmm_sampler *s, int32_t kind, hmm_mlp *mlp) {
+    if (!s) return HMM_EINVAL;
+    if (kind != HMM_PROPOSAL_RW && kind != HMM_PROPOSAL_MLP) return HMM_EINVAL;
+    if (kind == HMM_PROPOSAL_MLP) {
+        if (!mlp || mlp_dim(mlp) != s->D) return HMM_EINVAL;
+        if (!s->mx) {
+            const int C = s->C, D = s->D, H = mlp_hidden(mlp);
+            cudaError_t e = cudaMalloc(&s->mx, sizeof(float) * C * D);
+            if (e == cudaSuccess) e = cudaMalloc(&s->ma1, sizeof(float) * C * H);
+            if (e == cudaSuccess) e = cudaMalloc(&s->ma2, sizeof(float) * C * H);
+            if (e == cudaSuccess) e = cudaMalloc(&s->net_f, sizeof(float) * C * 2 * D);
+            if (e == cudaSuccess) e = cudaMalloc(&s->net_r, sizeof(float) * C * 2 * D);
+            if (e == cudaSuccess) e = cudaMalloc(&s->logq, sizeof(double) * C);
+            if (e == cudaSuccess) e = cudaMalloc(&s->qcorr, sizeof(double) * C);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return HMM_ENOMEM;
+            }
+        } else if (mlp_hidden(mlp) != mlp_hidden(s->mlp ? s->mlp : mlp)) {
+            return HMM_EINVAL;  // buffers were sized for another hidden width
+        }
+    }
+    // the captured iteration no longer matches: capture again on the next call
+    if (s->own) cudaStreamSynchronize(s->own);
+    if (s->exec) {
+        cudaGraphExecDestroy(s->exec);
+        s->exec = nullptr;
+    }
+    if (s->graph) {
+        cudaGraphDestroy(s->graph);
+        s->graph = nullptr;
+    }
+    s->graph_failed = 0;
+    s->kind = kind;
+    s->mlp = kind == HMM_PROPOSAL_MLP ? mlp : nullptr;
+    return HMM_OK;
 }
 
 int hmm_sampler_launches_per_iter(const hmm_sampler *s) { return s ? s->launches_per_iter : -1; }
