@@ -253,9 +253,9 @@ def main():
         from paper_2003_03508_gb300 import build as _b
         with open(tpath) as f:
             tr = json.load(f)
-        key = f"{args.precision}:K{args.K}:T{args.T}:P{args.n_prop}"
+        key = f"{args.precision}:K{args.K}:T{args.T}:P{args.n_prop}:L{L}"
         ent = tr.get(key)
-        if ent and ent.get("build") == _b.library_path().stem:
+        if ent and ent.get("kernel_digest") == _b.kernel_digest("hmm_chunk_tc.cu", "hmm_chunk_simt.cu"):
             traffic = ent["bytes_per_launch"]
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic, "kernel": "hmm chunk products",

@@ -47,6 +47,17 @@ def _digest(extra=()) -> str:
     return h.hexdigest()[:12]
 
 
+def kernel_digest(*names: str) -> str:
+    """Hash of the named csrc files, the internal header and the flags: it
+    changes exactly when the code of those kernels can have changed."""
+    h = hashlib.sha1()
+    for n in sorted(set(names) | {"hmm_internal.cuh"}):
+        h.update(n.encode())
+        h.update((CSRC / n).read_bytes())
+    h.update(" ".join(f for f in ARCH + NVCC_FLAGS if not f.startswith("-I")).encode())
+    return h.hexdigest()[:12]
+
+
 def library_path() -> Path:
     return BUILD / f"libhmm_gb300_{_digest()}.so"
 
