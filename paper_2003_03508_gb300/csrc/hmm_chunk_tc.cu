@@ -38,6 +38,7 @@ namespace {
 
 constexpr int TC_M = 128;
 constexpr int NISS = 4;  // MMA issuer warps (warps 0..3)
+constexpr int FAST_R = 4;  // renormalisation interval of the unrolled fast path
 constexpr long long SPIN_LIMIT_CYCLES = 4000000000LL;  // about 2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -297,6 +298,49 @@ __device__ __forceinline__ float chunk_max(float v, int lane) {
     }
 }
 
+// Per-row power-of-two renormalisation of one row of KP values: the row
+// maximum is brought into [1, 2) and its exponent added to `expo`. Returns
+// the maximum before scaling (0 for an all-zero row). A non-finite maximum
+// of a live row raises ENUMERIC.
+template <int KP>
+__device__ __forceinline__ float renorm_row(float *a, int &expo, bool live, unsigned *status) {
+    float m4[KP / 4];
+#pragma unroll
+    for (int j = 0; j < KP / 4; ++j) m4[j] = max3f(max3f(a[4 * j], a[4 * j + 1], a[4 * j + 2]), a[4 * j + 3], 0.0f);
+#pragma unroll
+    for (int s = KP / 8; s > 0; s >>= 1)
+#pragma unroll
+        for (int j = 0; j < s; ++j) m4[j] = fmaxf(m4[j], m4[j + s]);
+    const float mx = m4[0];
+    if (mx > 0.0f) {
+        if (!isfinite(mx) && live) atomicOr(status, ST_ENUMERIC);
+        int rr = float_exponent(mx);
+        rr = rr < -126 ? -126 : (rr > 126 ? 126 : rr);
+        const unsigned long long s2 = pack2(pow2f(-rr), pow2f(-rr));
+#pragma unroll
+        for (int j = 0; j < KP / 2; ++j) {
+            unsigned long long pp = mul2(pack2(a[2 * j], a[2 * j + 1]), s2);
+            unpack2(pp, a[2 * j], a[2 * j + 1]);
+        }
+        expo += rr;
+    }
+    return mx;
+}
+
+// column scale of one row by the step's emission factors (KP values in shared memory)
+template <int KP>
+__device__ __forceinline__ void scale_row(float *a, const float *d) {
+    const float4 *dv = reinterpret_cast<const float4 *>(d);
+#pragma unroll
+    for (int j4 = 0; j4 < KP / 4; ++j4) {
+        const float4 dd = dv[j4];
+        unsigned long long p0 = mul2(pack2(a[4 * j4], a[4 * j4 + 1]), pack2(dd.x, dd.y));
+        unsigned long long p1 = mul2(pack2(a[4 * j4 + 2], a[4 * j4 + 3]), pack2(dd.z, dd.w));
+        unpack2(p0, a[4 * j4], a[4 * j4 + 1]);
+        unpack2(p1, a[4 * j4 + 2], a[4 * j4 + 3]);
+    }
+}
+
 template <int KP, int PREC, int G, int E>
 struct TcCfg {
     static constexpr int ESZ = PREC == HMM_PREC_BF16 ? 2 : 4;  // bytes per operand element
@@ -527,7 +571,105 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
                 cp_async_commit();
             }
 
-            for (int t = 0; t < steps; ++t) {
+            const bool fast = (renorm == FAST_R) && (steps % FAST_R == 0);
+            bool bad = false;
+            if (fast) {
+                // ---- fast path: four steps per trip, renormalisation on the fourth ----
+                for (int t0 = 0; t0 < steps && !bad; t0 += FAST_R) {
+                    const int bsel = (t0 / C::WIN) & 1;
+                    if ((t0 & (C::WIN - 1)) == 0) {
+                        if (t0 > 0) {
+#pragma unroll
+                            for (int u = 0; u < C::GPW; ++u) {
+#pragma unroll
+                                for (int v = 0; v < C::NWIN; ++v) {
+                                    const int s = t0 + C::WIN + jl + KP * v;
+                                    if (s < len[u]) cp_async8(smem_u32(win_ptr(u, bsel ^ 1) + jl + KP * v), packed + pstart[u] + s);
+                                }
+                            }
+                            cp_async_commit();
+                        }
+                        cp_async_wait1();
+                        __syncwarp();
+                    }
+#pragma unroll
+                    for (int r = 0; r < FAST_R; ++r) {
+                        const int t = t0 + r;
+                        const int w = (t0 & (C::WIN - 1)) + r;
+                        int Et[C::GPW];
+#pragma unroll
+                        for (int u = 0; u < C::GPW; ++u) {
+                            const float2 o = win_ptr(u, bsel)[w];
+                            const float dx = o.x - mux, dy = o.y - muy;
+                            float l = fmaf(qa * dx, dx, fmaf(qb * dx, dy, fmaf(qc * dy, dy, ctr)));
+                            l = isnan(o.x) ? cno : l;
+                            const float m = chunk_max<KP>(l, lane);
+                            float mf;
+                            const int e = round_to_int(m, mf);
+                            const bool ok = m >= -(float)EXP_LIMIT;
+                            Et[u] = ok ? e : 0;
+                            const float d = ex2_approx(l - mf);
+                            if (!ok && m != -INFINITY && t < len[u]) atomicOr(status, ST_ENUMERIC);
+                            sD[u * 32 + lane] = ok ? d : 0.0f;
+                        }
+                        __syncwarp();
+#pragma unroll
+                        for (int u = 0; u < C::GPW; ++u) {
+                            const int g = team + E * u;
+                            if (!(glive >> u & 1u)) continue;
+                            const bool okw = __all_sync(0xffffffffu, mbar_wait(&full[g], (full_par >> g) & 1u, abort_flag, status));
+                            full_par ^= 1u << g;
+                            if (!okw) {
+                                bad = true;
+                                break;
+                            }
+                            tc_fence_after();
+                            float a[KP];
+#pragma unroll
+                            for (int c16 = 0; c16 < KP / 16; ++c16) tmem_ld16(tm_row + g * KP + c16 * 16, a + c16 * 16);
+                            tmem_wait_ld();
+                            scale_row<KP>(a, sD + u * 32 + half * KP);
+                            expo[u] += Et[u];
+                            float mx = 1.0f;
+                            if (r == FAST_R - 1) mx = renorm_row<KP>(a, expo[u], t < len[u], status);
+                            if (t + 1 == len[u]) {
+                                // this lane's chunk ends here: renormalise (if not done) and write it
+                                if (r != FAST_R - 1) mx = renorm_row<KP>(a, expo[u], true, status);
+                                const size_t jj = (size_t)q * n_chunks + (size_t)b * per_item + g * C::CPG + cs;
+                                float4 *dst = reinterpret_cast<float4 *>(A0 + jj * KP * KP + (size_t)i * KP);
+#pragma unroll
+                                for (int j4 = 0; j4 < KP / 4; ++j4)
+                                    dst[j4] = make_float4(a[4 * j4], a[4 * j4 + 1], a[4 * j4 + 2], a[4 * j4 + 3]);
+                                e0[jj * KP + i] = (mx > 0.0f) ? expo[u] : ZERO_ROW_EXP32;
+                            }
+                            if (t + 1 < steps) {
+                                // next A operand row (finished chunks' rows carry values nobody reads)
+                                uint32_t *wv = reinterpret_cast<uint32_t *>(a);
+                                if constexpr (C::ESZ == 4) {
+#pragma unroll
+                                    for (int c = 0; c < KP; ++c) wv[c] = to_tf32_bits(a[c]);
+                                } else {
+#pragma unroll
+                                    for (int c = 0; c < KP / 2; ++c) {
+                                        __nv_bfloat162 bb = __floats2bfloat162_rn(a[2 * c], a[2 * c + 1]);
+                                        wv[c] = *reinterpret_cast<uint32_t *>(&bb);
+                                    }
+                                }
+                                tmem_st_row<C::KA>(tm_row + C::A_COL0 + g * C::KA, wv);
+                                tmem_wait_st();
+                                tc_fence_before();
+                                __syncwarp();
+                                if (lane == 0) mbar_arrive(&empty[g]);
+                            }
+                        }
+                        if (bad) break;
+                    }
+                }
+            }
+            int rcount = renorm;
+            for (int t = 0; t < steps && !fast; ++t) {
+                const bool rn_step = (--rcount == 0);
+                if (rn_step) rcount = renorm;
                 const int w = t % C::WIN;
                 const int bsel = (t / C::WIN) & 1;
                 if (w == 0) {
@@ -591,38 +733,11 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
                     }
                     if (okw && t < len[u]) {
                         // Step 2 fused: column scale by D_t (pairs)
-                        const float4 *dv = reinterpret_cast<const float4 *>(sD + u * 32 + half * KP);
-#pragma unroll
-                        for (int j4 = 0; j4 < KP / 4; ++j4) {
-                            const float4 dd = dv[j4];
-                            unsigned long long p0 = mul2(pack2(a[4 * j4], a[4 * j4 + 1]), pack2(dd.x, dd.y));
-                            unsigned long long p1 = mul2(pack2(a[4 * j4 + 2], a[4 * j4 + 3]), pack2(dd.z, dd.w));
-                            unpack2(p0, a[4 * j4], a[4 * j4 + 1]);
-                            unpack2(p1, a[4 * j4 + 2], a[4 * j4 + 3]);
-                        }
+                        scale_row<KP>(a, sD + u * 32 + half * KP);
                         expo[u] += Et[u];
                         const bool last = (t + 1 == len[u]);
-                        if ((t + 1) % renorm == 0 || last) {
-                            float m4[KP / 4];
-#pragma unroll
-                            for (int j = 0; j < KP / 4; ++j) m4[j] = max3f(max3f(a[4 * j], a[4 * j + 1], a[4 * j + 2]), a[4 * j + 3], 0.0f);
-#pragma unroll
-                            for (int s = KP / 8; s > 0; s >>= 1)
-#pragma unroll
-                                for (int j = 0; j < s; ++j) m4[j] = fmaxf(m4[j], m4[j + s]);
-                            const float mx = m4[0];
-                            if (mx > 0.0f) {
-                                if (!isfinite(mx)) atomicOr(status, ST_ENUMERIC);
-                                int rr = float_exponent(mx);
-                                rr = rr < -126 ? -126 : (rr > 126 ? 126 : rr);
-                                const unsigned long long s2 = pack2(pow2f(-rr), pow2f(-rr));
-#pragma unroll
-                                for (int j = 0; j < KP / 2; ++j) {
-                                    unsigned long long pp = mul2(pack2(a[2 * j], a[2 * j + 1]), s2);
-                                    unpack2(pp, a[2 * j], a[2 * j + 1]);
-                                }
-                                expo[u] += rr;
-                            }
+                        if (rn_step || last) {
+                            const float mx = renorm_row<KP>(a, expo[u], true, status);
                             if (last) {
                                 const size_t jj = (size_t)q * n_chunks + (size_t)b * per_item + (team + E * u) * C::CPG + cs;
                                 float4 *dst = reinterpret_cast<float4 *>(A0 + jj * KP * KP + (size_t)i * KP);
