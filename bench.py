@@ -14,7 +14,11 @@ Also reported on the same line:
                 buffers, host->device inputs and device->host results inside
                 the timed region);
   roofline      the chunk-product kernel against its peak;
-  cpu_baseline  the FP64 CPU oracle on a bounded sample, on the host cores.
+  cpu_baseline  the FP64 CPU oracle on a bounded sample, on the host cores;
+  mcmc          effective samples per second of the log posterior, the
+                random-walk sampler against the learned (MLP) proposal trained
+                on the random walk's own history, same chains and iterations
+                (K=16, 512 chains; T reduced so the run stays within a minute).
 
 ``--impl reference`` times the CPU oracle instead (rank 0 only).
 Multi-GPU (torchrun): every rank evaluates its own n_prop proposals (weak
@@ -55,6 +59,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-mcmc", action="store_true")
+    ap.add_argument("--mcmc-K", type=int, default=16)
+    ap.add_argument("--mcmc-T", type=int, default=16384)
+    ap.add_argument("--mcmc-chains", type=int, default=512)
+    ap.add_argument("--mcmc-iters", type=int, default=1000)
     return ap.parse_args()
 
 
@@ -139,9 +148,9 @@ def cpu_baseline(inputs, n_sample, cores):
     prm = inputs["params"]
     sub = type(prm)(*(a[:n_sample] for a in prm.as_tuple()))
     t0 = time.perf_counter()
-    oracle.loglik_batched(sub, inputs["xy"], inputs["tremor"], inputs["offsets"], n_threads=cores)
+    ref = oracle.loglik_batched(sub, inputs["xy"], inputs["tremor"], inputs["offsets"], n_threads=cores)
     dt = time.perf_counter() - t0
-    return n_sample / dt, dt
+    return n_sample / dt, dt, np.asarray(ref, dtype=np.float64)
 
 
 def run_reference(args):
@@ -155,7 +164,7 @@ def run_reference(args):
         cpu_baseline(inputs, cores, cores)
     times = []
     for _ in range(args.steps):
-        _, dt = cpu_baseline(inputs, cores, cores)
+        _, dt, _ = cpu_baseline(inputs, cores, cores)
         times.append(dt)
     ms = 1e3 * statistics.mean(times)
     value = cores / (ms / 1e3)
@@ -255,7 +264,7 @@ def main():
             tr = json.load(f)
         key = f"{args.precision}:K{args.K}:T{args.T}:P{args.n_prop}:L{L}"
         ent = tr.get(key)
-        if ent and ent.get("kernel_digest") == _b.kernel_digest("hmm_chunk_tc.cu", "hmm_chunk_simt.cu"):
+        if ent and ent.get("kernel_digest") == _b.kernel_digest("hmm_chunk_tc.cu", "hmm_chunk_simt.cu", "hmm_tc_common.cuh"):
             traffic = ent["bytes_per_launch"]
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic, "kernel": "hmm chunk products",
@@ -297,6 +306,7 @@ def main():
                                "precision": "fp32_simt", "n_prop": n_plain, "ms_per_step": pms}
         d = (out[:n_plain] - pout).abs().max().item()
         result["plain_gpu"]["max_abs_diff_vs_tc"] = d
+        plain_out = pout.cpu().numpy()
 
     # end to end through the host-buffer entry point
     if not args.no_e2e:
@@ -327,13 +337,30 @@ def main():
                          "steps": n_e2e, "ms_per_step": ems / n_e2e,
                          "matches_device_result": bool(np.array_equal(hout.numpy(), out.cpu().numpy()))}
 
+    if rank == 0 and not args.no_mcmc:
+        from paper_2003_03508_gb300 import chains
+        mopts = api.make_opts(precision="tf32", recheck_fp32=1)
+        result["mcmc"] = chains.rw_vs_learned(K=args.mcmc_K, T=args.mcmc_T, chains=args.mcmc_chains,
+                                              seed=args.seed, n_measure=args.mcmc_iters, opts=mopts)
+        result["mcmc"]["likelihood"] = "tf32 tensor cores, accepted proposals rechecked in fp32"
+
     if rank == 0 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         n_sample = min(args.n_prop, cores)
-        v, dt = cpu_baseline(inputs, n_sample, cores)
+        v, dt, ref = cpu_baseline(inputs, n_sample, cores)
         result["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": min(cores, n_sample), "kind": "oracle",
                                   "sample": f"{n_sample} of the {args.n_prop} proposals, full T={args.T}, "
                                             f"one proposal per thread ({dt:.1f} s wall)"}
+        # log-likelihood error of the timed path against the FP64 oracle on that sample
+        got = out[:n_sample].cpu().numpy()
+        rel = np.abs(got - ref) / np.abs(ref)
+        result["error_vs_oracle"] = {"dtype": args.precision, "proposals": int(n_sample),
+                                     "max_rel": float(rel.max()), "max_abs": float(np.abs(got - ref).max()),
+                                     "log_lik_mean": float(ref.mean())}
+        if "plain_gpu" in result:
+            pg = plain_out[:min(n_sample, plain_out.shape[0])]
+            relp = np.abs(pg - ref[:pg.shape[0]]) / np.abs(ref[:pg.shape[0]])
+            result["plain_gpu"]["max_rel_vs_oracle"] = float(relp.max())
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:

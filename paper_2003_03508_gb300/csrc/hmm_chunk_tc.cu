@@ -28,353 +28,11 @@
 // Every wait is bounded: a wait that runs out sets the context's ETIMEOUT
 // status bit and an abort flag; all warps then drain (in-flight copies and
 // MMAs) and return, and the TMEM is freed.
-#include <cuda_bf16.h>
-
-#include "hmm_internal.cuh"
+#include "hmm_tc_common.cuh"
 
 namespace hmm {
 
 namespace {
-
-constexpr int TC_M = 128;
-constexpr int NISS = 4;  // MMA issuer warps (warps 0..3)
-constexpr int FAST_R = 4;  // renormalisation interval of the unrolled fast path
-constexpr long long SPIN_LIMIT_CYCLES = 4000000000LL;  // about 2 s at 2 GHz
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// non-blocking probe of one phase (never suspends the thread)
-__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait on one phase of an mbarrier. Returns false (and raises the
-// CTA's abort flag and the ETIMEOUT status bit) if it runs out, or at once
-// if another warp already aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
-                                          unsigned *status) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    for (;;) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (clock64() - t0 > SPIN_LIMIT_CYCLES) {
-            *abort_flag = 1;
-            atomicOr(status, ST_ETIMEOUT);
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor, canonical K-major layout without swizzle:
-// 8-row x 16-byte core matrices, `lbo` bytes between core matrices along K,
-// `sbo` bytes between 8-row groups.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
-    return d;                // base offset 0, no swizzle
-}
-
-// Instruction descriptor: FP32 accumulate, A and B K-major, M = 128, N = n.
-template <int PREC>
-__host__ __device__ constexpr uint32_t instr_desc(int n) {
-    // A/B format: TF32 = 2 (kind::tf32), BF16 = 1 (kind::f16)
-    return (1u << 4) | ((PREC == HMM_PREC_BF16 ? 1u : 2u) << 7) |
-           ((PREC == HMM_PREC_BF16 ? 1u : 2u) << 10) | ((uint32_t)(n >> 3) << 17) |
-           ((uint32_t)(TC_M >> 4) << 24);
-}
-
-// D (TMEM) = A (TMEM) x B (shared memory), or D += A x B
-template <int PREC>
-__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
-                                       uint32_t accumulate) {
-    if constexpr (PREC == HMM_PREC_BF16) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
-            : "memory");
-    } else {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
-            : "memory");
-    }
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     smem_u32(bar))
-                 : "memory");
-}
-
-// 32 lanes x 16 columns of 32-bit TMEM data into 16 registers per thread
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 32 lanes x 32 columns of 32-bit TMEM data into 32 registers per thread
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// one thread's row of NC consecutive 32-bit TMEM columns (NC = 16 or 32)
-template <int NC>
-__device__ __forceinline__ void tmem_ld_row(uint32_t taddr, float *v) {
-    static_assert(NC == 16 || NC == 32, "row width");
-    if constexpr (NC == 32) tmem_ld32(taddr, v);
-    else tmem_ld16(taddr, v);
-}
-
-__device__ __forceinline__ void tmem_wait_ld() {
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// 16 registers per thread into 32 lanes x 16 columns of TMEM
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *r) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
-        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
-        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
-        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t *r) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
-                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t *r) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
-        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
-        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
-        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
-        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
-        "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]),
-        "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
-        : "memory");
-}
-
-// one thread's row of NC consecutive 32-bit TMEM columns (NC = 8, 16 or 32)
-template <int NC>
-__device__ __forceinline__ void tmem_st_row(uint32_t taddr, const uint32_t *r) {
-    static_assert(NC == 8 || NC == 16 || NC == 32, "row width");
-    if constexpr (NC == 8) tmem_st8(taddr, r);
-    else if constexpr (NC == 16) tmem_st16(taddr, r);
-    else tmem_st32(taddr, r);
-}
-
-__device__ __forceinline__ void tmem_wait_st() {
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
-
-// FP32 -> TF32 operand, round to nearest with ties away from zero: add half a
-// TF32 unit in the last place to the bit pattern (integer pipe; overflow
-// rounds to infinity as it should). The tensor core reads a TF32 operand from
-// the top 19 bits and ignores the 13 low bits, so they need not be cleared;
-// the parity tests pin this (identical results with and without the mask).
-__device__ __forceinline__ uint32_t to_tf32_bits(float x) {
-    return __float_as_uint(x) + 0x1000u;
-}
-
-// nearest integer to m (|m| < 2^22) and the same value as a float, without
-// the conversion pipe: add and subtract 1.5 * 2^23
-__device__ __forceinline__ int round_to_int(float m, float &mf) {
-    const float magic = 12582912.0f;
-    const float t = __fadd_rn(m, magic);
-    mf = __fsub_rn(t, magic);
-    return __float_as_int(t) - 0x4B400000;
-}
-
-// 2^x on the special-function unit (FTZ: results below 2^-126 flush to 0)
-__device__ __forceinline__ float ex2_approx(float x) {
-    float r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
-                 : "memory");
-}
-
-__device__ __forceinline__ void named_barrier(int id, int nthreads) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
-// barrier over the epilogue warps that also ORs a predicate across them
-__device__ __forceinline__ bool named_barrier_or(int id, int nthreads, bool pred) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.or.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)pred), "r"(id), "r"(nthreads)
-        : "memory");
-    return r != 0;
-}
-
-// packed FP32 pair helpers (sm_100+ f32x2 arithmetic)
-__device__ __forceinline__ unsigned long long pack2(float a, float b) {
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void unpack2(unsigned long long v, float &a, float &b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
-    unsigned long long r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ float max3f(float a, float b, float c) {
-    float r;
-    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-}
-
-__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-// maximum over the KP lanes of each chunk (KP = 32: whole warp, KP = 16: halves)
-template <int KP>
-__device__ __forceinline__ float chunk_max(float v, int lane) {
-    if constexpr (KP == 32) {
-        float m;
-        asm("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(m) : "f"(v));
-        return m;
-    } else {
-        float lo = lane < 16 ? v : -INFINITY, hi = lane < 16 ? -INFINITY : v, m0, m1;
-        asm("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(m0) : "f"(lo));
-        asm("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(m1) : "f"(hi));
-        return lane < 16 ? m0 : m1;
-    }
-}
-
-// Per-row power-of-two renormalisation of one row of KP values: the row
-// maximum is brought into [1, 2) and its exponent added to `expo`. Returns
-// the maximum before scaling (0 for an all-zero row). A non-finite maximum
-// of a live row raises ENUMERIC.
-template <int KP>
-__device__ __forceinline__ float renorm_row(float *a, int &expo, bool live, unsigned *status) {
-    float m4[KP / 4];
-#pragma unroll
-    for (int j = 0; j < KP / 4; ++j) m4[j] = max3f(max3f(a[4 * j], a[4 * j + 1], a[4 * j + 2]), a[4 * j + 3], 0.0f);
-#pragma unroll
-    for (int s = KP / 8; s > 0; s >>= 1)
-#pragma unroll
-        for (int j = 0; j < s; ++j) m4[j] = fmaxf(m4[j], m4[j + s]);
-    const float mx = m4[0];
-    if (mx > 0.0f) {
-        if (!isfinite(mx) && live) atomicOr(status, ST_ENUMERIC);
-        int rr = float_exponent(mx);
-        rr = rr < -126 ? -126 : (rr > 126 ? 126 : rr);
-        const unsigned long long s2 = pack2(pow2f(-rr), pow2f(-rr));
-#pragma unroll
-        for (int j = 0; j < KP / 2; ++j) {
-            unsigned long long pp = mul2(pack2(a[2 * j], a[2 * j + 1]), s2);
-            unpack2(pp, a[2 * j], a[2 * j + 1]);
-        }
-        expo += rr;
-    }
-    return mx;
-}
-
-// column scale of one row by the step's emission factors (KP values in shared
-// memory). Scalar multiplies: they issue to both FP32 pipes, where the paired
-// f32x2 form measured slower here.
-template <int KP>
-__device__ __forceinline__ void scale_row(float *a, const float *d) {
-    const float4 *dv = reinterpret_cast<const float4 *>(d);
-#pragma unroll
-    for (int j4 = 0; j4 < KP / 4; ++j4) {
-        const float4 dd = dv[j4];
-        a[4 * j4] *= dd.x;
-        a[4 * j4 + 1] *= dd.y;
-        a[4 * j4 + 2] *= dd.z;
-        a[4 * j4 + 3] *= dd.w;
-    }
-}
 
 template <int KP, int PREC, int G, int E>
 struct TcCfg {
@@ -855,10 +513,11 @@ template <> struct TcTile<16, HMM_PREC_BF16> { static constexpr int G = 16, E = 
 
 bool chunk_tc_supported(int K, int precision) {
     if (precision != HMM_PREC_TF32 && precision != HMM_PREC_TF32_SPLIT && precision != HMM_PREC_BF16) return false;
-    return K >= 1 && K <= 32;
+    return K >= 1 && K <= 80;
 }
 
 int chunk_tc_chunks_per_item(int KP, int precision) {
+    if (KP > 32) return chunk_tc_wide_chunks_per_item(KP, precision);
 #define HMM_TC_PER_ITEM(KPV, PRECV) \
     if (KP == KPV && precision == PRECV) return TcTile<KPV, PRECV>::G * (TC_M / KPV);
     HMM_TC_PER_ITEM(16, HMM_PREC_TF32)
@@ -877,6 +536,9 @@ cudaError_t launch_chunk_tc(int n_prop, int n_chunks, int L, int renorm, int pre
                             cudaStream_t st) {
     (void)L;
     if (n_chunks == 0 || n_prop == 0) return cudaSuccess;
+    if (lay.KP > 32)
+        return launch_chunk_tc_wide(n_prop, n_chunks, renorm, precision, lay, cblock, chunks, packed, A0, e0,
+                                    status, st);
 #define HMM_TC_CASE(KPV, PRECV)                                                                              \
     if (lay.KP == KPV && precision == PRECV)                                                                  \
         return launch_tc_t<KPV, PRECV, TcTile<KPV, PRECV>::G, TcTile<KPV, PRECV>::E>(n_prop, n_chunks, renorm, \

@@ -1,13 +1,14 @@
 """Parity of the tensor-core (tcgen05) chunk products with the FP64 oracle.
 
 Tolerance for TF32 / BF16 / TF32-split chunk products: |d| <= 1e-4 |log L|
-(relative in log L), with an absolute floor of 1e-3 for tiny sequences. The
-error budget behind it: the running product is rounded to the operand type
-every step (unbiased, O(sqrt(T) u) in log L with u = 2^-11 for TF32, 2^-9
-for BF16), and P is rounded once (a bias of at most ~T u / sqrt(K) in log L;
-removed to O(u^2) by the hi+lo split used for BF16 and TF32-split). Each
-test also reports the observed error so the per-dtype figures can be read
-off the log.
+(relative in log L), or, for short sequences whose |log L| is small, the
+per-T absolute bound |d| <= 8 sqrt(T) u (u = 2^-11 for TF32 operands, 2^-9
+for BF16), plus 1e-3. The error budget behind it: the running product is
+rounded to the operand type every step (round to nearest, unbiased, so the
+errors add up like a random walk: O(sqrt(T) u) in log L), and P is rounded
+once (a bias of at most ~T u / sqrt(K) in log L; removed to O(u^2) by the
+hi+lo split used for BF16 and TF32-split). Each test also reports the
+observed error so the per-dtype figures can be read off the log.
 """
 import math
 
@@ -22,6 +23,12 @@ pytestmark = pytest.mark.gpu
 
 TC_REL, TC_ABS = 1e-4, 1e-3
 PRECS = ["tf32", "tf32_split", "bf16"]
+UNIT = {"tf32": 2.0 ** -11, "tf32_split": 2.0 ** -11, "bf16": 2.0 ** -9}
+
+
+def tol(prec, T, ref):
+    """Allowed |log L error| for a tensor-core precision on T observations."""
+    return max(TC_REL * abs(ref), 8.0 * math.sqrt(max(T, 1)) * UNIT[prec]) + TC_ABS
 
 
 def _run(api, prm, xy, tremor, **opt):
@@ -33,7 +40,7 @@ def _run(api, prm, xy, tremor, **opt):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("K", [1, 4, 16, 17, 25, 32])
+@pytest.mark.parametrize("K", [1, 4, 16, 17, 25, 32, 33, 48, 49, 64, 65, 80])
 def test_tc_parity_sizes(cuda_lib, K, prec):
     rng = np.random.default_rng(2000 + K)
     prm = synth.random_params(K, rng)
@@ -44,7 +51,7 @@ def test_tc_parity_sizes(cuda_lib, K, prec):
         got = _run(cuda_lib, prm, obs.xy, obs.tremor, precision=prec, chunk_len=L)
         err = abs(got - ref)
         print(f"K={K} {prec} L={L}: rel err {err / abs(ref):.2e}")
-        assert err <= TC_REL * abs(ref) + TC_ABS, (K, prec, L, got, ref)
+        assert err <= tol(prec, T, ref), (K, prec, L, got, ref)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -55,20 +62,33 @@ def test_tc_small_T(cuda_lib, prec, T):
     obs = synth.sample_observations(prm, T, rng)
     ref = oracle.loglik(prm, obs.xy, obs.tremor)
     got = _run(cuda_lib, prm, obs.xy, obs.tremor, precision=prec, chunk_len=64)
-    assert abs(got - ref) <= TC_REL * abs(ref) + TC_ABS, (T, got, ref)
+    assert abs(got - ref) <= tol(prec, T, ref), (T, got, ref)
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_tc_batched_segments(cuda_lib, prec):
+@pytest.mark.parametrize("K", [64, 80])
+@pytest.mark.parametrize("T", [0, 1, 2, 65, 130])
+def test_tc_wide_small_T(cuda_lib, prec, K, T):
+    rng = np.random.default_rng(700 + T + K)
+    prm = synth.random_params(K, rng)
+    obs = synth.sample_observations(prm, T, rng)
+    ref = oracle.loglik(prm, obs.xy, obs.tremor)
+    got = _run(cuda_lib, prm, obs.xy, obs.tremor, precision=prec, chunk_len=64)
+    assert abs(got - ref) <= tol(prec, T, ref), (K, T, got, ref)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("K", [32, 48, 64, 80])
+def test_tc_batched_segments(cuda_lib, prec, K):
     api = cuda_lib
-    d = synth.batched_inputs(K=32, T=80_000, n_prop=12, seed=5, n_seg=7)
+    d = synth.batched_inputs(K=K, T=80_000, n_prop=12, seed=5, n_seg=7)
     ctx = api.default_context()
     got = ctx.hmm_loglik_batched(*api.to_device(d["params"]), d["offsets"],
                                  torch.from_numpy(d["xy"]).cuda(), torch.from_numpy(d["tremor"]).cuda(),
                                  opts=api.make_opts(precision=prec, chunk_len=256)).cpu().numpy()
     ref = oracle.loglik_batched(d["params"], d["xy"], d["tremor"], d["offsets"], n_threads=4)
     rel = np.abs(got - ref) / np.abs(ref)
-    print(f"{prec} batched max rel err {rel.max():.2e}")
+    print(f"K={K} {prec} batched max rel err {rel.max():.2e}")
     assert np.all(rel <= TC_REL), rel
 
 
@@ -118,3 +138,56 @@ def test_bench_workload_sampled(cuda_lib):
     print("sampled rel err tf32", np.abs(tc[pick] - ref) / np.abs(ref), "fp32", np.abs(fp[pick] - ref) / np.abs(ref))
     assert np.all(np.abs(tc[pick] - ref) <= TC_REL * np.abs(ref))
     assert np.all(np.abs(fp[pick] - ref) <= 1e-6 * np.abs(ref))
+
+
+@pytest.mark.parametrize("K", [64, 80])
+def test_precision_sweep_wide_full_size(cuda_lib, K):
+    """K=64 and K=80, T=2^22, 128 proposals (the precision-sweep workload):
+    FP32-SIMT, TF32, TF32-split and BF16 chunk products on every proposal,
+    the FP64 oracle on two sampled proposals; FP32 recheck agreement on all."""
+    api = cuda_lib
+    d = synth.batched_inputs(K=K, T=1 << 22, n_prop=128, seed=11)
+    ctx = api.default_context()
+    dev = api.to_device(d["params"])
+    xy = torch.from_numpy(d["xy"]).cuda()
+    fl = torch.from_numpy(d["tremor"]).cuda()
+    res = {}
+    for prec in ["fp32"] + PRECS:
+        res[prec] = ctx.hmm_loglik_batched(*dev, d["offsets"], xy, fl,
+                                           opts=api.make_opts(precision=prec)).cpu().numpy()
+        assert ctx.hmm_status() == api.HMM_OK
+    pick = [5, 100]
+    sub = type(d["params"])(*(a[pick] for a in d["params"].as_tuple()))
+    ref = oracle.loglik_batched(sub, d["xy"], d["tremor"], d["offsets"], n_threads=2)
+    for prec, v in res.items():
+        rel = np.abs(v[pick] - ref) / np.abs(ref)
+        print(f"K={K} T=2^22 {prec}: sampled rel err {rel.max():.2e}")
+        assert np.all(rel <= (1e-6 if prec == "fp32" else TC_REL)), (prec, rel)
+        if prec != "fp32":
+            assert np.all(np.abs(v - res["fp32"]) <= TC_REL * np.abs(res["fp32"]))
+
+
+def test_uneven_segments_full_size(cuda_lib):
+    """K=32, 256 proposals, 64 segments of log-uniform length (1e3..1e6 steps,
+    about 2^24 in total) shared by all proposals (the batched-MCMC workload):
+    FP32-SIMT then TF32, both on every proposal; the FP64 oracle on two
+    sampled proposals."""
+    api = cuda_lib
+    d = synth.batched_inputs(K=32, T=1 << 24, n_prop=256, seed=3, n_seg=64)
+    assert len(d["offsets"]) == 65
+    ctx = api.default_context()
+    dev = api.to_device(d["params"])
+    xy = torch.from_numpy(d["xy"]).cuda()
+    fl = torch.from_numpy(d["tremor"]).cuda()
+    fp = ctx.hmm_loglik_batched(*dev, d["offsets"], xy, fl, opts=api.make_opts(precision="fp32")).cpu().numpy()
+    assert ctx.hmm_status() == api.HMM_OK
+    tc = ctx.hmm_loglik_batched(*dev, d["offsets"], xy, fl, opts=api.make_opts(precision="tf32")).cpu().numpy()
+    assert ctx.hmm_status() == api.HMM_OK
+    assert np.all(np.abs(tc - fp) <= TC_REL * np.abs(fp))
+    pick = [17, 230]
+    sub = type(d["params"])(*(a[pick] for a in d["params"].as_tuple()))
+    ref = oracle.loglik_batched(sub, d["xy"], d["tremor"], d["offsets"], n_threads=2)
+    print("64 segments, 2^24 steps: rel err fp32", np.abs(fp[pick] - ref) / np.abs(ref),
+          "tf32", np.abs(tc[pick] - ref) / np.abs(ref))
+    assert np.all(np.abs(fp[pick] - ref) <= 1e-6 * np.abs(ref))
+    assert np.all(np.abs(tc[pick] - ref) <= TC_REL * np.abs(ref))
