@@ -196,3 +196,39 @@ def test_learned_proposal_vs_random_walk(cuda_lib):
     assert info["losses"][-100:].mean() < info["losses"][:20].mean()
     assert gain_it > 1.1
     ls.close(); rw.close(); mlp.close()
+
+
+def test_learned_sampler_full_size(cuda_lib):
+    """The learned-proposal workload's launch: K=16 (d=351), T=2^20, 512
+    chains, TF32 likelihood with FP32 recheck, a 2x256 network. A few random-
+    walk iterations, a short training run on their trace, then learned
+    iterations; the stored log likelihood of sampled chains is the FP64
+    oracle's, and the stored log posterior is that plus the prior."""
+    api = cuda_lib
+    from paper_2003_03508_gb300 import chains
+    K, T, C = 16, 1 << 20, 512
+    prob = chains.tremor_problem(K, T, C, seed=9)
+    pr = api.make_prior(K, alpha_P=0.5)
+    step = torch.from_numpy(chains.base_steps(K) * 0.0625).cuda()
+    s = api.Sampler(K, prob["theta0"], step, 9, [0, T], prob["xy"], prob["tremor"], prior=pr,
+                    opts=api.make_opts(precision="tf32", recheck_fp32=1))
+    _, hist = s.step(24, trace_theta=True)
+    X, Y = learned.history_pairs(hist, lag=4)
+    m = api.MLP(s.D, hidden=256, seed=2)
+    m.fit_scaling(X, Y, lam=0.05)
+    losses = m.train(X, Y, 50, batch=512, lr=1e-3, seed=3).cpu().numpy()
+    assert np.all(np.isfinite(losses))
+    m.set_lambda(0.05, 0.5)
+    s.set_proposal(m)
+    lp_tr, _ = s.step(3, trace_logpost=True)
+    th, lp, ll, na = s.state()
+    assert torch.all(torch.isfinite(lp_tr)) and torch.all(torch.isfinite(ll))
+    (pi, P, p, mu, cov), lprior = api.theta_to_params(th, K, pr)
+    assert torch.allclose(lp, ll + lprior, rtol=0, atol=1e-6 * float(ll.abs().max()))
+    pick = [3, 411]
+    prm = synth.HMMParams(*(t[pick].cpu().numpy() for t in (pi, P, p, mu, cov)))
+    ref = oracle.loglik_batched(prm, prob["obs"].xy, prob["obs"].tremor, np.array([0, T], np.int64), n_threads=2)
+    got = ll[pick].cpu().numpy()
+    print("K=16 T=2^20 512 chains: stored log L rel err vs oracle", np.abs(got - ref) / np.abs(ref))
+    assert np.all(np.abs(got - ref) <= 1e-6 * np.abs(ref))
+    s.close(); m.close()
