@@ -67,6 +67,27 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x_ms, world, device):
+    """The job's time is the slowest rank's: all-reduce MAX (identity on one rank)."""
+    if world == 1:
+        return float(x_ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, total_ms):
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / (total_ms / 1e3)
+
+
+def rank_seed(seed, rank):
+    """Each rank evaluates its own proposals (weak scaling, no data exchange)."""
+    return seed + 1000 * rank
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -201,7 +222,7 @@ def main():
         if world > 1:
             dist.barrier()
 
-    inputs = synth.batched_inputs(K=args.K, T=args.T, n_prop=args.n_prop, seed=args.seed + 1000 * rank)
+    inputs = synth.batched_inputs(K=args.K, T=args.T, n_prop=args.n_prop, seed=rank_seed(args.seed, rank))
     ctx = api.Context(local)
     dev = api.to_device(inputs["params"])
     xy = torch.from_numpy(inputs["xy"]).cuda()
@@ -243,13 +264,9 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in evs]
     prof, ncalls = ctx.hmm_profile_read()
     ctx.hmm_profile_enable(False)
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, "cuda")
     ms_per_step = total_ms / args.steps
-    value = world * args.n_prop * args.steps / (total_ms / 1e3)
+    value = job_rate(args.n_prop * args.steps, world, total_ms)
     status = ctx.hmm_status()
 
     # roofline of the chunk-product kernel (its phase is one launch per step)
@@ -326,13 +343,9 @@ def main():
             ctx.hmm_loglik_batched_host(*hp, offs, hxy, hfl, opts=opts, out=hout)
         e1.record(stream)
         torch.cuda.synchronize()
-        ems = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ems], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
         h2d = sum(a.numel() * a.element_size() for a in hp) + hxy.numel() * 4 + hfl.numel()
-        result["e2e"] = {"value": world * args.n_prop * n_e2e / (ems / 1e3), "unit": UNIT,
+        result["e2e"] = {"value": job_rate(args.n_prop * n_e2e, world, ems), "unit": UNIT,
                          "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8 * args.n_prop,
                          "steps": n_e2e, "ms_per_step": ems / n_e2e,
                          "matches_device_result": bool(np.array_equal(hout.numpy(), out.cpu().numpy()))}
