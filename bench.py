@@ -60,10 +60,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-mcmc", action="store_true")
+    ap.add_argument("--no-peaks", action="store_true")
     ap.add_argument("--mcmc-K", type=int, default=16)
     ap.add_argument("--mcmc-T", type=int, default=16384)
     ap.add_argument("--mcmc-chains", type=int, default=512)
-    ap.add_argument("--mcmc-iters", type=int, default=1000)
+    ap.add_argument("--mcmc-iters", type=int, default=10000)
     return ap.parse_args()
 
 
@@ -86,6 +87,35 @@ def job_rate(units_per_rank, world, total_ms):
 def rank_seed(seed, rank):
     """Each rank evaluates its own proposals (weak scaling, no data exchange)."""
     return seed + 1000 * rank
+
+
+def measured_peaks(device):
+    """This GPU's FP32 FFMA rate (library kernel) and cuBLAS TF32 GEMM rate
+    (torch.matmul with TF32 allowed, 8192^3, best of 10 after warm-up)."""
+    import torch
+    from paper_2003_03508_gb300 import api
+    out = {"fp32_ffma_tflops": api.measure_fp32_peak(device)}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        n = 8192
+        a = torch.randn(n, n, device="cuda")
+        b = torch.randn(n, n, device="cuda")
+        for _ in range(3):
+            a @ b
+        best = float("inf")
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        out["tf32_cublas_tflops"] = 2.0 * n ** 3 / (best / 1e3) / 1e12
+        del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    return out
 
 
 def peaks():
@@ -349,6 +379,12 @@ def main():
                          "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8 * args.n_prop,
                          "steps": n_e2e, "ms_per_step": ems / n_e2e,
                          "matches_device_result": bool(np.array_equal(hout.numpy(), out.cpu().numpy()))}
+
+    if rank == 0 and not args.no_peaks:
+        pm = measured_peaks(local)
+        result["peaks_measured"] = pm
+        if args.precision in ("tf32", "tf32_split"):
+            result["roofline"]["frac_vs_measured_tf32_cublas"] = achieved / pm["tf32_cublas_tflops"]
 
     if rank == 0 and not args.no_mcmc:
         from paper_2003_03508_gb300 import chains

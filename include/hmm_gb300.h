@@ -382,6 +382,15 @@ int hmm_sampler_set_proposal(hmm_sampler *sampler, int32_t kind, hmm_mlp *mlp);
 int hmm_loglik_noalloc(const hmm_params *params, const hmm_obs *obs, double *out_dev,
                        void *stream);
 
+/*
+ * Measured FP32 FFMA throughput of `device` in TFLOP/s (written to *tflops,
+ * a host pointer): the roofline denominator of the FP32-SIMT chunk kernel,
+ * from a kernel of independent FFMA chains timed with CUDA events (best of
+ * three after a warm-up, about 0.1 s). Allocates a small scratch buffer.
+ * A measurement helper; the paper has no counterpart.
+ */
+int hmm_measure_fp32_peak(int device, double *tflops);
+
 #ifdef __cplusplus
 }
 #endif

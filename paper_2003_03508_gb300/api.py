@@ -77,6 +77,7 @@ _I32 = ctypes.c_int32
 # name -> (restype, argtypes); exactly the functions declared in include/hmm_gb300.h
 SIGNATURES = {
     "hmm_opts_default": (None, [ctypes.POINTER(hmm_opts)]),
+    "hmm_measure_fp32_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "hmm_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int]),
     "hmm_destroy": (ctypes.c_int, [_VP]),
     "hmm_last_error": (ctypes.c_char_p, [_VP]),
@@ -539,3 +540,12 @@ def to_device(prm, device="cuda"):
     """HMMParams (numpy) -> tuple of CUDA float32 tensors (pi, P, p_tremor, mu, cov)."""
     return tuple(torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(device)
                  for a in prm.as_tuple())
+
+
+def measure_fp32_peak(device: int = 0) -> float:
+    """Measured FP32 FFMA TFLOP/s of the device (library kernel)."""
+    v = ctypes.c_double(0.0)
+    rc = load_library().hmm_measure_fp32_peak(int(device), ctypes.byref(v))
+    if rc != HMM_OK:
+        raise HMMError(rc, "hmm_measure_fp32_peak failed")
+    return float(v.value)

@@ -68,13 +68,36 @@ def _timed_run(sampler, n_iter, trace_theta=False):
     return lp, th, e0.elapsed_time(e1) / 1e3
 
 
-def rw_vs_learned(K=16, T=16384, chains=512, seed=0, burn=2000, history=200, lag=20, hidden=256,
+def invariant_summaries(theta_trace, K):
+    """Label-invariant scalar traces [n_iter, C, 2K] of a theta trace: the
+    sorted tremor-probability logits (sorting logits sorts p_k) and the
+    sorted x coordinates of the state means."""
+    o = K * (K - 1) + (K - 1)
+    w = theta_trace[:, :, o:o + K]
+    mx = theta_trace[:, :, o + K:o + 3 * K:2]
+    return torch.cat([torch.sort(w, dim=2).values, torch.sort(mx, dim=2).values], dim=2)
+
+
+def _ess_summary(lp, summ, K):
+    out = {"log_post": ess.ess_chains(lp.cpu().numpy())}
+    summ = summ.cpu().numpy()
+    vals = np.array([ess.ess_chains(summ[:, :, j]) for j in range(summ.shape[2])])
+    out["summaries_min"] = float(vals.min())
+    out["summaries_median"] = float(np.median(vals))
+    return out
+
+
+def rw_vs_learned(K=16, T=16384, chains=512, seed=0, burn=3000, history=200, lag=20, hidden=256,
                   train_steps=2000, batch=512, lr=2e-3, n_measure=1000, alpha_P=0.5,
-                  target_accept=0.25, opts=None):
+                  target_accept=0.25, opts=None, cross=True):
     """Tune and burn in the random walk, train the learned proposal on its
-    history, then run both samplers for n_measure iterations from the same
-    states and report effective samples per second of the log posterior
-    (Geyer initial monotone sequence estimator, summed over chains)."""
+    history (cross=True: pairs of different chains at the same iteration,
+    else pairs `lag` iterations apart in one chain), pick its step factor and
+    drift factor by the expected squared jump distance of short pilots, then
+    run both samplers for n_measure iterations from the same states and
+    report effective samples per second of the log posterior and of the
+    label-invariant summaries (Geyer initial monotone sequence estimator,
+    summed over chains)."""
     prob = tremor_problem(K, T, chains, seed)
     pr = api.make_prior(K, alpha_P=alpha_P)
     step0 = base_steps(K)
@@ -83,8 +106,9 @@ def rw_vs_learned(K=16, T=16384, chains=512, seed=0, burn=2000, history=200, lag
         return api.Sampler(K, th.contiguous(), torch.from_numpy(step).cuda(), s, [0, T], prob["xy"],
                            prob["tremor"], prior=pr, opts=opts)
 
-    # step multiplier whose acceptance is closest to the target: halve from 1
-    # until the acceptance passes the target (it grows as the step shrinks)
+    # step multiplier whose acceptance is closest to the target: shrink by
+    # sqrt(2) from 1 until the acceptance passes the target (it grows as the
+    # step shrinks)
     best = None
     mult = 1.0
     while mult >= 1.0 / 256:
@@ -96,7 +120,7 @@ def rw_vs_learned(K=16, T=16384, chains=512, seed=0, burn=2000, history=200, lag
             best = (mult, acc)
         if acc >= target_accept:
             break
-        mult *= 0.5
+        mult *= 0.5 ** 0.5
     step = step0 * best[0]
     rw = make(prob["theta0"], step, seed + 2)
     rw.step(burn)
@@ -107,29 +131,41 @@ def rw_vs_learned(K=16, T=16384, chains=512, seed=0, burn=2000, history=200, lag
     ls = make(th_now, step, seed + 3)
     mlp, info = learned.fit_learned_proposal(ls, hist, lag=lag, hidden=hidden, train_steps=train_steps,
                                              batch=batch, lr=lr, seed=seed + 4, target_accept=target_accept,
-                                             lams=tuple(0.8 * 0.5 ** k for k in range(8)))
+                                             lams=(1.0, 0.5, 0.25, 0.12, 0.06), gammas=(1.0, 0.5, 0.2, 0.0),
+                                             select="esjd", pilot_iters=100, cross=cross)
     fit_s = time.perf_counter() - t0
     del hist
 
     na0 = rw.state()[3].clone()
-    lp_rw, _, t_rw = _timed_run(rw, n_measure)
+    lp_rw, th, t_rw = _timed_run(rw, n_measure, trace_theta=True)
     acc_rw = float((rw.state()[3] - na0).double().mean().item()) / n_measure
+    sm_rw = invariant_summaries(th, K)
+    del th
     na0 = ls.state()[3].clone()
-    lp_ml, _, t_ml = _timed_run(ls, n_measure)
+    lp_ml, th, t_ml = _timed_run(ls, n_measure, trace_theta=True)
     acc_ml = float((ls.state()[3] - na0).double().mean().item()) / n_measure
-    e_rw = ess.ess_chains(lp_rw.cpu().numpy())
-    e_ml = ess.ess_chains(lp_ml.cpu().numpy())
+    sm_ml = invariant_summaries(th, K)
+    del th
+    s_rw = _ess_summary(lp_rw, sm_rw, K)
+    s_ml = _ess_summary(lp_ml, sm_ml, K)
+    e_rw, e_ml = s_rw["log_post"], s_ml["log_post"]
     finite = bool(torch.isfinite(lp_ml).all().item() and torch.isfinite(lp_rw).all().item())
     out = {
         "K": K, "T": T, "chains": chains, "theta_dim": api.theta_dim(K), "iterations": n_measure,
         "rw": {"ess": e_rw, "seconds": t_rw, "ess_per_s": e_rw / t_rw, "accept": acc_rw,
-               "step_mult": best[0], "ms_per_iter": 1e3 * t_rw / n_measure},
+               "step_mult": best[0], "ms_per_iter": 1e3 * t_rw / n_measure,
+               "ess_summaries_min": s_rw["summaries_min"], "ess_summaries_median": s_rw["summaries_median"]},
         "learned": {"ess": e_ml, "seconds": t_ml, "ess_per_s": e_ml / t_ml, "accept": acc_ml,
-                    "lam": info["lam"], "gamma": info["gamma"], "hidden": hidden,
-                    "ms_per_iter": 1e3 * t_ml / n_measure},
+                    "lam": info["lam"], "gamma": info["gamma"], "hidden": hidden, "lam_pilots": info["pilot"],
+                    "ms_per_iter": 1e3 * t_ml / n_measure,
+                    "ess_summaries_min": s_ml["summaries_min"], "ess_summaries_median": s_ml["summaries_median"],
+                    "ess_per_s_training_amortised": e_ml / (t_ml + fit_s)},
         "gain_ess_per_s": (e_ml / t_ml) / (e_rw / t_rw),
         "gain_ess_per_iter": e_ml / e_rw,
-        "training": {"pairs": info["n_pairs"], "steps": train_steps, "seconds": fit_s,
+        "gain_summaries_min_per_s": (s_ml["summaries_min"] / t_ml) / (s_rw["summaries_min"] / t_rw),
+        "gain_summaries_median_per_s": (s_ml["summaries_median"] / t_ml) / (s_rw["summaries_median"] / t_rw),
+        "training": {"pairs": info["n_pairs"], "pairs_kind": "cross-chain" if cross else f"lag {lag}",
+                     "steps": train_steps, "seconds": fit_s,
                      "loss_first": float(np.mean(info["losses"][:20])),
                      "loss_last": float(np.mean(info["losses"][-100:]))},
         "finite": finite,

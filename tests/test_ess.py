@@ -31,3 +31,15 @@ def test_ess_chains_sums():
     rng = np.random.default_rng(2)
     tr = rng.standard_normal((50_000, 4))
     assert abs(ess.ess_chains(tr) - 200_000) / 200_000 < 0.1
+
+
+def test_esjd_of_a_known_walk():
+    """Expected squared jump distance: a walk with unit steps in every one of
+    D coordinates, scaled by 2, has ESJD = D / 4."""
+    import torch
+    from paper_2003_03508_gb300 import learned
+    n, C, D = 50, 3, 7
+    steps = torch.ones(n, C, D)
+    steps[::2] *= -1.0
+    th = torch.cumsum(steps, dim=0)
+    assert abs(learned.esjd(th, torch.full((D,), 2.0)) - D / 4) < 1e-6
