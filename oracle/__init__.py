@@ -18,7 +18,7 @@ from pathlib import Path
 import numpy as np
 
 _HERE = Path(__file__).resolve().parent
-_SRC = [_HERE / "hmm_oracle.c", _HERE / "mcmc_oracle.c", _HERE / "mlp_oracle.c"]
+_SRC = [_HERE / "hmm_oracle.c", _HERE / "mcmc_oracle.c", _HERE / "mlp_oracle.c", _HERE / "twalk_oracle.c"]
 _BUILD = _HERE / "_build"
 _lib = None
 
@@ -63,6 +63,13 @@ _i32 = ctypes.POINTER(ctypes.c_int32)
 
 
 def _declare(L):
+    if hasattr(L, "oracle_loglik"):
+        _declare_loglik(L)
+    if hasattr(L, "oracle_philox4x32_10"):
+        _declare_mcmc(L)
+
+
+def _declare_loglik(L):
     sig = [ctypes.c_int, _f, _f, _f, _f, _f, ctypes.c_int64, _f, _u8, ctypes.c_int]
     for name in ("oracle_loglik", "oracle_loglik_backward", "oracle_loglik_ld",
                  "oracle_loglik_bruteforce"):
@@ -76,8 +83,6 @@ def _declare(L):
                                         ctypes.c_int, _i64, _f, _u8, ctypes.c_int, _d,
                                         ctypes.c_int]
     L.oracle_loglik_batched.restype = None
-    if hasattr(L, "oracle_philox4x32_10"):
-        _declare_mcmc(L)
 
 
 class OraclePrior(ctypes.Structure):
@@ -108,6 +113,13 @@ def _declare_mcmc(L):
         L.oracle_adam_step.argtypes = [ctypes.c_size_t, _d, _d, _d, _d, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.oracle_adam_step.restype = None
+    if hasattr(L, "oracle_twalk_propose"):
+        _ip = ctypes.POINTER(ctypes.c_int)
+        L.oracle_twalk_propose.argtypes = [ctypes.c_int, _f, _f, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                           _ip, _ip, _ip, _f, _d, _d]
+        L.oracle_twalk_propose.restype = None
+        L.oracle_twalk_gauss_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _d, _f, _f, _f, _d]
+        L.oracle_twalk_gauss_run.restype = None
 
 
 def default_prior(K, box=(0.0, 300.0, 0.0, 150.0)):
@@ -271,3 +283,41 @@ def adam_step(params, grad, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
         assert a.dtype == np.float64 and a.flags.c_contiguous
     lib().oracle_adam_step(params.size, _dp(params), _dp(grad), _dp(m), _dp(v), int(t), lr, b1, b2, eps)
     return params, m, v
+
+
+TWALK_KERNELS = ("traverse", "walk", "blow", "hop")
+
+
+def twalk_propose(x, xp, seed, chain, it):
+    """One t-walk proposal (twalk_oracle.c): (side, kernel name, n_phi, y float32, W)."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    xp = np.ascontiguousarray(np.asarray(xp, dtype=np.float32))
+    n = x.size
+    y = np.zeros(n, dtype=np.float32)
+    work = np.zeros(6 * n + 1, dtype=np.float64)
+    side, kern, m = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    W = ctypes.c_double(0.0)
+    lib().oracle_twalk_propose(int(n), x.ctypes.data_as(_f), xp.ctypes.data_as(_f), ctypes.c_uint64(seed),
+                               ctypes.c_uint32(chain), ctypes.c_uint32(it), ctypes.byref(side), ctypes.byref(kern),
+                               ctypes.byref(m), y.ctypes.data_as(_f), ctypes.byref(W),
+                               work.ctypes.data_as(_d))
+    return side.value, TWALK_KERNELS[kern.value], m.value, y, W.value
+
+
+TWALK_MIXTURE = (0.4918, 0.9836, 0.9918)
+
+
+def twalk_gauss_run(x0, xp0, n_iter, seed, kernels=TWALK_MIXTURE, _L=None):
+    """A t-walk run on the standard normal target (twalk_oracle.c): samples
+    [n_iter, n]. `kernels`: cumulative probabilities of traverse, walk, blow
+    (the rest is hop); e.g. (0, 0, 1) runs the blow kernel alone."""
+    F = np.ascontiguousarray(np.asarray(kernels, dtype=np.float64))
+    x0 = np.ascontiguousarray(np.asarray(x0, dtype=np.float32))
+    xp0 = np.ascontiguousarray(np.asarray(xp0, dtype=np.float32))
+    n = x0.size
+    out = np.zeros((n_iter, n), dtype=np.float32)
+    work = np.zeros(6 * n + 2 * n + 2, dtype=np.float64)  # 6n doubles + 3n floats
+    (_L or lib()).oracle_twalk_gauss_run(int(n), int(n_iter), ctypes.c_uint64(seed), F.ctypes.data_as(_d),
+                                         x0.ctypes.data_as(_f),
+                                 xp0.ctypes.data_as(_f), out.ctypes.data_as(_f), work.ctypes.data_as(_d))
+    return out
