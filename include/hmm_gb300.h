@@ -277,6 +277,7 @@ int hmm_sampler_graph_active(const hmm_sampler *sampler);
 
 #define HMM_PROPOSAL_RW 0   /* theta' = theta + step * N(0, I)                        */
 #define HMM_PROPOSAL_MLP 1  /* theta' ~ q(. | theta) given by an hmm_mlp (see below)   */
+#define HMM_PROPOSAL_TWALK 2 /* the t-walk: two points per chain (hmm_sampler_set_twalk) */
 
 typedef struct hmm_mlp hmm_mlp;
 
@@ -381,6 +382,28 @@ int hmm_sampler_set_proposal(hmm_sampler *sampler, int32_t kind, hmm_mlp *mlp);
  */
 int hmm_loglik_noalloc(const hmm_params *params, const hmm_obs *obs, double *out_dev,
                        void *stream);
+
+/*
+ * The t-walk (Christen & Fox, "A general purpose sampling algorithm for
+ * continuous distributions (the t-walk)", Bayesian Analysis 2010), the
+ * sampler the paper runs (Section "Monte Carlo Markov Chains"). Every chain
+ * keeps a second point x'; an iteration moves one of the two (probability
+ * 1/2 each) on a random coordinate subset (each coordinate with probability
+ * min(D, 4)/D, drawn again while empty) by the traverse (0.4918), walk
+ * (0.4918), blow (0.0082) or hop (0.0082) kernel with the other point as
+ * reference (a_w = 1.5, a_t = 6), and accepts by the Metropolis-Hastings rule
+ * with each kernel's factor. The step sizes of hmm_sampler_create are not
+ * used. The chain's reported state, traces and recheck are the first point.
+ *
+ * hmm_sampler_set_twalk: theta2 = the second points (device [n_chains][D],
+ * copied; must differ from the first points in every coordinate for the
+ * blow and hop kernels to move); evaluates their log posterior on `stream`
+ * (synchronised before returning) and switches the sampler to the t-walk.
+ * hmm_sampler_twalk_state: the second points and their log posteriors
+ * (device outputs, either may be NULL).
+ */
+int hmm_sampler_set_twalk(hmm_sampler *sampler, const float *theta2, void *stream);
+int hmm_sampler_twalk_state(hmm_sampler *sampler, float *theta2_out, double *logpost2_out, void *stream);
 
 /*
  * Measured FP32 FFMA throughput of `device` in TFLOP/s (written to *tflops,

@@ -34,6 +34,7 @@ HMM_INIT_TRANSITION_FIRST = 1
 
 HMM_PROPOSAL_RW = 0
 HMM_PROPOSAL_MLP = 1
+HMM_PROPOSAL_TWALK = 2
 
 PRECISIONS = {"fp32": HMM_PREC_FP32_SIMT, "tf32": HMM_PREC_TF32, "bf16": HMM_PREC_BF16,
               "tf32_split": HMM_PREC_TF32_SPLIT}
@@ -115,6 +116,8 @@ SIGNATURES = {
     "hmm_mlp_set_lambda": (ctypes.c_int, [_VP, ctypes.c_float, ctypes.c_float]),
     "hmm_mlp_train": (ctypes.c_int, [_VP, _I32, _VP, _VP, _I32, _I32, ctypes.c_float, ctypes.c_uint64, _VP, _VP]),
     "hmm_sampler_set_proposal": (ctypes.c_int, [_VP, _I32, _VP]),
+    "hmm_sampler_set_twalk": (ctypes.c_int, [_VP, _VP, _VP]),
+    "hmm_sampler_twalk_state": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "hmm_loglik_noalloc": (ctypes.c_int, [ctypes.POINTER(hmm_params), ctypes.POINTER(hmm_obs), _VP, _VP]),
     "hmm_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "hmm_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
@@ -429,6 +432,27 @@ class Sampler:
         if rc != HMM_OK:
             raise HMMError(rc, "hmm_sampler_set_proposal failed")
         self._mlp = mlp
+
+    def set_twalk(self, theta2, stream=None):
+        """Switch to the t-walk with second points theta2 [C, D] (CUDA float32)."""
+        theta2 = theta2.contiguous()
+        _dev(theta2, torch.float32, "theta2")
+        if tuple(theta2.shape) != (self.C, self.D):
+            raise ValueError(f"theta2 must be [{self.C}, {self.D}]")
+        rc = self.lib.hmm_sampler_set_twalk(self.h, theta2.data_ptr(), _stream_ptr(stream))
+        if rc != HMM_OK:
+            raise HMMError(rc, "hmm_sampler_set_twalk failed")
+        self._mlp = None
+
+    def twalk_state(self, stream=None):
+        """(second points [C, D], their log posteriors [C]) of a t-walk sampler."""
+        th = torch.empty(self.C, self.D, device="cuda")
+        lp = torch.empty(self.C, dtype=torch.float64, device="cuda")
+        rc = self.lib.hmm_sampler_twalk_state(self.h, th.data_ptr(), lp.data_ptr(), _stream_ptr(stream))
+        if rc != HMM_OK:
+            raise HMMError(rc, "hmm_sampler_twalk_state failed")
+        torch.cuda.synchronize()
+        return th, lp
 
 
 class MLP:

@@ -18,6 +18,15 @@
 // (Box-Muller, cos/sin) and (index, chain, iteration, 1) for the acceptance
 // uniform, so a run is reproducible and any draw can be recomputed.
 //
+// The t-walk (HMM_PROPOSAL_TWALK; Christen & Fox, Bayesian Analysis 2010, the
+// sampler the paper uses) keeps a second point per chain and moves one of the
+// two per iteration: a random coordinate subset (each coordinate with
+// probability min(D, 4)/D, drawn again while empty) by the traverse (0.4918),
+// walk (0.4918), blow (0.0082) or hop (0.0082) kernel, with the reference
+// point the other one. Its draws use further Philox streams: side, kernel and
+// beta uniforms (counter word 2), walk uniforms (3), blow/hop normals (4),
+// subset attempt a (9 + a).
+//
 // One iteration = propose (+ transform) kernel, the batched likelihood, the
 // accept kernel, and a one-thread kernel that advances the iteration counter
 // kept in device memory. After a first, ordinary iteration the sampler
@@ -70,6 +79,22 @@ __device__ double normal_draw(uint64_t seed, uint32_t chain, uint32_t iter, uint
 
 __device__ double uniform_draw(uint64_t seed, uint32_t chain, uint32_t iter, uint32_t index) {
     uint32_t c[4] = {index, chain, iter, 1u};
+    philox(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    return u01(c[0]);
+}
+
+// draws on a numbered stream (the fourth counter word): normals use the
+// stream itself, uniforms stream + 1, as in the two functions above
+__device__ double normal_draw_s(uint64_t seed, uint32_t stream, uint32_t chain, uint32_t iter, uint32_t index) {
+    uint32_t c[4] = {index / 2, chain, iter, stream};
+    philox(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const double rad = sqrt(-2.0 * log(u01(c[0])));
+    const double ang = 6.283185307179586476925286766559 * u01(c[1]);
+    return (index & 1) ? rad * sin(ang) : rad * cos(ang);
+}
+
+__device__ double uniform_draw_s(uint64_t seed, uint32_t stream, uint32_t chain, uint32_t iter, uint32_t index) {
+    uint32_t c[4] = {index, chain, iter, stream + 1};
     philox(c, (uint32_t)seed, (uint32_t)(seed >> 32));
     return u01(c[0]);
 }
@@ -293,6 +318,187 @@ __global__ void __launch_bounds__(TPB) accept_kernel(int D, uint64_t seed, const
             ctl->trace_theta[(k * gridDim.x + c) * D + d] = theta[(size_t)c * D + d];
 }
 
+// ---- t-walk ----
+constexpr double TW_AW = 1.5, TW_AT = 6.0, TW_N1 = 4.0;
+constexpr double TW_F_TRAVERSE = 0.4918, TW_F_WALK = 0.9836, TW_F_BLOW = 0.9918;
+constexpr int TW_MAX_ATTEMPTS = 64;
+enum { TW_TRAVERSE = 0, TW_WALK = 1, TW_BLOW = 2, TW_HOP = 3 };
+
+__device__ double block_max(double v, double *red) {
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = TPB / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// One t-walk proposal per chain (one CTA): picks the moving point, the
+// kernel and the coordinate subset, writes the proposal theta' (float), the
+// log of its acceptance factor besides the target ratio (W, -inf for a
+// degenerate move), the side that moves, and theta' -> parameters + log
+// density. Shared memory: theta' (D doubles), the reduction buffer, the
+// subset (D bytes).
+__global__ void __launch_bounds__(TPB) propose_twalk_kernel(int K, int D, const float *__restrict__ x,
+                                                            const float *__restrict__ x2, uint64_t seed,
+                                                            const Ctl *__restrict__ ctl, Prior pr, float *theta_prop,
+                                                            double *W_out, int *side_out, float *pi, float *P,
+                                                            float *p, float *mu, float *cov, double *logprior) {
+    extern __shared__ double sm[];
+    double *th = sm;
+    double *red = sm + D;
+    unsigned char *phi = reinterpret_cast<unsigned char *>(sm + D + TPB);
+    __shared__ int s_side, s_kern;
+    __shared__ double s_beta;
+    const int c = blockIdx.x;
+    const uint32_t it = (uint32_t)ctl->iter;
+    if (threadIdx.x == 0) {
+        s_side = uniform_draw_s(seed, 1, (uint32_t)c, it, 0) < 0.5 ? 0 : 1;
+        const double uk = uniform_draw_s(seed, 1, (uint32_t)c, it, 1);
+        s_kern = uk < TW_F_TRAVERSE ? TW_TRAVERSE : uk < TW_F_WALK ? TW_WALK : uk < TW_F_BLOW ? TW_BLOW : TW_HOP;
+        const double u1 = uniform_draw_s(seed, 1, (uint32_t)c, it, 2), u2 = uniform_draw_s(seed, 1, (uint32_t)c, it, 3);
+        s_beta = u1 < (TW_AT - 1.0) / (2.0 * TW_AT) ? pow(u2, 1.0 / (TW_AT + 1.0)) : pow(u2, 1.0 / (1.0 - TW_AT));
+    }
+    __syncthreads();
+    const int side = s_side, kern = s_kern;
+    const float *h = (side == 0 ? x : x2) + (size_t)c * D;
+    const float *r = (side == 0 ? x2 : x) + (size_t)c * D;
+    // the coordinate subset, drawn again while empty
+    const double pphi = (D < TW_N1 ? (double)D : TW_N1) / (double)D;
+    int m = 0;
+    for (int a = 0; a < TW_MAX_ATTEMPTS && m == 0; ++a) {
+        double cnt = 0.0;
+        for (int d = threadIdx.x; d < D; d += TPB) {
+            const unsigned char f = uniform_draw_s(seed, 8 + a, (uint32_t)c, it, (uint32_t)d) < pphi;
+            phi[d] = f;
+            cnt += f;
+        }
+        m = (int)block_sum(cnt, red);
+    }
+    if (m == 0) {  // practically unreachable: move every coordinate
+        for (int d = threadIdx.x; d < D; d += TPB) phi[d] = 1;
+        m = D;
+    }
+    __syncthreads();
+    double w = 0.0;
+    if (kern == TW_TRAVERSE) {
+        const double beta = s_beta;
+        for (int d = threadIdx.x; d < D; d += TPB) {
+            const double hv = h[d], rv = r[d];
+            th[d] = (double)(float)(phi[d] ? rv + beta * (rv - hv) : hv);
+        }
+        w = (m - 2) * log(beta);
+    } else if (kern == TW_WALK) {
+        for (int d = threadIdx.x; d < D; d += TPB) {
+            const double hv = h[d], rv = r[d];
+            double yv = hv;
+            if (phi[d]) {
+                const double u = uniform_draw_s(seed, 2, (uint32_t)c, it, (uint32_t)d);
+                const double z = TW_AW / (1.0 + TW_AW) * (-1.0 + 2.0 * u + TW_AW * u * u);
+                yv = hv + (hv - rv) * z;
+            }
+            th[d] = (double)(float)yv;
+        }
+    } else {
+        double sf = 0.0;
+        for (int d = threadIdx.x; d < D; d += TPB)
+            if (phi[d]) sf = fmax(sf, fabs((double)r[d] - (double)h[d]));
+        sf = block_max(sf, red);
+        const bool blow = kern == TW_BLOW;
+        if (!(sf > 0.0)) {
+            w = -INFINITY;
+            for (int d = threadIdx.x; d < D; d += TPB) th[d] = h[d];
+        } else {
+            const double sc = blow ? sf : sf / 3.0;
+            for (int d = threadIdx.x; d < D; d += TPB)
+                th[d] = (double)(float)(phi[d] ? (blow ? (double)r[d] : (double)h[d]) +
+                                                     sc * normal_draw_s(seed, 4, (uint32_t)c, it, (uint32_t)d)
+                                               : (double)h[d]);
+            __syncthreads();
+            // densities of the rounded proposal both ways (the 2 pi terms cancel)
+            double sb = 0.0;
+            for (int d = threadIdx.x; d < D; d += TPB)
+                if (phi[d]) sb = fmax(sb, fabs((double)r[d] - th[d]));
+            sb = block_max(sb, red);
+            if (!(sb > 0.0)) {
+                w = -INFINITY;
+            } else {
+                const double sfw = blow ? sf : sf / 3.0, sbw = blow ? sb : sb / 3.0;
+                double q = 0.0;
+                for (int d = threadIdx.x; d < D; d += TPB)
+                    if (phi[d]) {
+                        const double hv = h[d], yv = th[d], rv = r[d];
+                        const double rb = blow ? (hv - rv) / sbw : (hv - yv) / sbw;  // reverse: x from y
+                        const double rf = blow ? (yv - rv) / sfw : (yv - hv) / sfw;  // forward: y from x
+                        q += -0.5 * rb * rb + 0.5 * rf * rf;
+                    }
+                q = block_sum(q, red);
+                w = q - m * log(sbw) + m * log(sfw);
+            }
+        }
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < D; d += TPB) theta_prop[(size_t)c * D + d] = (float)th[d];
+    if (threadIdx.x == 0) {
+        W_out[c] = w;
+        side_out[c] = side;
+    }
+    __syncthreads();
+    const double lp = transform(K, th, pr, pi + (size_t)c * K, P + (size_t)c * K * K, p + (size_t)c * K,
+                                mu + (size_t)c * 2 * K, cov + (size_t)c * 3 * K, red);
+    if (threadIdx.x == 0) logprior[c] = lp;
+}
+
+// t-walk decision: accept when log u < (log L' + log pi') - (log L + log pi)
+// of the moving point + W; the accepted proposal replaces that point. The
+// traces record the first point.
+__global__ void __launch_bounds__(TPB) accept_twalk_kernel(int D, uint64_t seed, const Ctl *__restrict__ ctl,
+                                                           float *x, float *x2, const float *__restrict__ theta_prop,
+                                                           double *logpost, double *loglik, double *logprior,
+                                                           double *logpost2, double *loglik2, double *logprior2,
+                                                           const double *__restrict__ loglik_prop,
+                                                           const double *__restrict__ logprior_prop,
+                                                           const double *__restrict__ W, const int *__restrict__ side,
+                                                           unsigned long long *n_acc) {
+    const int c = blockIdx.x;
+    const uint32_t it = (uint32_t)ctl->iter;
+    __shared__ int acc;
+    const int sd = side[c];
+    if (threadIdx.x == 0) {
+        const double lpp = loglik_prop[c] + logprior_prop[c];
+        const double cur = sd == 0 ? logpost[c] : logpost2[c];
+        const double la = lpp - cur + W[c];
+        const double u = uniform_draw(seed, (uint32_t)c, it, 0u);
+        acc = (!isnan(lpp) && lpp > -INFINITY && W[c] > -INFINITY && log(u) < la) ? 1 : 0;
+        if (acc) {
+            if (sd == 0) {
+                logpost[c] = lpp;
+                loglik[c] = loglik_prop[c];
+                logprior[c] = logprior_prop[c];
+            } else {
+                logpost2[c] = lpp;
+                loglik2[c] = loglik_prop[c];
+                logprior2[c] = logprior_prop[c];
+            }
+            n_acc[c] += 1;
+        }
+    }
+    __syncthreads();
+    if (acc) {
+        float *dst = (sd == 0 ? x : x2) + (size_t)c * D;
+        for (int d = threadIdx.x; d < D; d += TPB) dst[d] = theta_prop[(size_t)c * D + d];
+    }
+    __syncthreads();
+    const unsigned long long k = ctl->iter - ctl->iter0;
+    if (ctl->trace_lp && threadIdx.x == 0) ctl->trace_lp[k * gridDim.x + c] = (float)logpost[c];
+    if (ctl->trace_theta)
+        for (int d = threadIdx.x; d < D; d += TPB)
+            ctl->trace_theta[(k * gridDim.x + c) * D + d] = x[(size_t)c * D + d];
+}
+
 __global__ void advance_kernel(Ctl *ctl) { ctl->iter += 1; }
 
 // replace the stored log likelihood of every chain by its FP32-SIMT value and
@@ -357,6 +563,10 @@ struct hmm_sampler {
     hmm_mlp *mlp = nullptr;
     float *mx = nullptr, *ma1 = nullptr, *ma2 = nullptr, *net_f = nullptr, *net_r = nullptr;
     double *logq = nullptr, *qcorr = nullptr;
+    // t-walk (HMM_PROPOSAL_TWALK): the second point of every chain
+    float *theta2 = nullptr;
+    double *logpost2 = nullptr, *loglik2 = nullptr, *logprior2 = nullptr, *tw_W = nullptr;
+    int *tw_side = nullptr;
     // iterations run on the sampler's own stream (the legacy default stream
     // cannot be captured), ordered against the caller's stream by events
     cudaStream_t own = nullptr;
@@ -389,6 +599,7 @@ static Prior to_prior(const hmm_prior *p, int K) {
 }
 
 static size_t smem_for(int D) { return sizeof(double) * ((size_t)D + TPB); }
+static size_t smem_twalk(int D) { return smem_for(D) + (size_t)D + 16; }
 
 extern "C" {
 
@@ -430,7 +641,8 @@ int hmm_sampler_destroy(hmm_sampler *s) {
     if (s->own) cudaStreamDestroy(s->own);
     void *bufs[] = {s->theta, s->theta_prop, s->step, s->pi, s->P, s->p, s->mu, s->cov, s->logpost, s->loglik,
                     s->logprior, s->loglik_prop, s->logprior_prop, s->n_acc, s->ctl, s->loglik32,
-                    s->recheck_maxdiff, s->mx, s->ma1, s->ma2, s->net_f, s->net_r, s->logq, s->qcorr};
+                    s->recheck_maxdiff, s->mx, s->ma1, s->ma2, s->net_f, s->net_r, s->logq, s->qcorr,
+                    s->theta2, s->logpost2, s->loglik2, s->logprior2, s->tw_W, s->tw_side};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete[] s->offs;
@@ -541,6 +753,10 @@ static int iteration(hmm_sampler *s, cudaStream_t st) {
         if (mlp_eval(s->mlp, C, s->theta_prop, s->mx, s->ma1, s->ma2, s->net_r, st)) return HMM_ECUDA;
         qcorr_kernel<<<C, TPB, 0, st>>>(D, s->theta, s->theta_prop, s->net_r, scale, lam, gam, s->logq, s->qcorr);
         extra = 2 * 4 + 1;  // two network evaluations (standardise + 3 GEMMs) and the q ratio
+    } else if (s->kind == HMM_PROPOSAL_TWALK) {
+        propose_twalk_kernel<<<C, TPB, smem_twalk(D), st>>>(K, D, s->theta, s->theta2, s->seed, s->ctl, s->prior,
+                                                             s->theta_prop, s->tw_W, s->tw_side, s->pi, s->P, s->p,
+                                                             s->mu, s->cov, s->logprior_prop);
     } else {
         propose_kernel<<<C, TPB, smem_for(D), st>>>(K, D, s->theta, s->step, s->seed, s->ctl, s->prior,
                                                      s->theta_prop, s->pi, s->P, s->p, s->mu, s->cov,
@@ -551,9 +767,14 @@ static int iteration(hmm_sampler *s, cudaStream_t st) {
                                 s->tremor, &s->opts, s->loglik_prop, st);
     if (rc) return rc;
     s->launches_per_iter = hmm_last_launch_count(s->lik) + 3 + extra;
-    accept_kernel<<<C, TPB, 0, st>>>(D, s->seed, s->ctl, s->theta, s->theta_prop, s->logpost, s->loglik,
-                                     s->logprior, s->loglik_prop, s->logprior_prop,
-                                     s->kind == HMM_PROPOSAL_MLP ? s->qcorr : nullptr, s->n_acc);
+    if (s->kind == HMM_PROPOSAL_TWALK)
+        accept_twalk_kernel<<<C, TPB, 0, st>>>(D, s->seed, s->ctl, s->theta, s->theta2, s->theta_prop, s->logpost,
+                                               s->loglik, s->logprior, s->logpost2, s->loglik2, s->logprior2,
+                                               s->loglik_prop, s->logprior_prop, s->tw_W, s->tw_side, s->n_acc);
+    else
+        accept_kernel<<<C, TPB, 0, st>>>(D, s->seed, s->ctl, s->theta, s->theta_prop, s->logpost, s->loglik,
+                                         s->logprior, s->loglik_prop, s->logprior_prop,
+                                         s->kind == HMM_PROPOSAL_MLP ? s->qcorr : nullptr, s->n_acc);
     advance_kernel<<<1, 1, 0, st>>>(s->ctl);
     return cudaGetLastError() == cudaSuccess ? HMM_OK : HMM_ECUDA;
 }
@@ -686,9 +907,55 @@ int hmm_sampler_state(hmm_sampler *s, float *theta_out, double *logpost_out, dou
     return e == cudaSuccess ? HMM_OK : HMM_ECUDA;
 }
 
+int hmm_sampler_set_twalk(hmm_sampler *s, const float *theta2, void *stream) {
+    if (!s || !theta2) return HMM_EINVAL;
+    const int C = s->C, K = s->K, D = s->D;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!s->theta2) {
+        cudaError_t e = cudaMalloc(&s->theta2, sizeof(float) * C * D);
+        if (e == cudaSuccess) e = cudaMalloc(&s->logpost2, sizeof(double) * C);
+        if (e == cudaSuccess) e = cudaMalloc(&s->loglik2, sizeof(double) * C);
+        if (e == cudaSuccess) e = cudaMalloc(&s->logprior2, sizeof(double) * C);
+        if (e == cudaSuccess) e = cudaMalloc(&s->tw_W, sizeof(double) * C);
+        if (e == cudaSuccess) e = cudaMalloc(&s->tw_side, sizeof(int) * C);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return HMM_ENOMEM;
+        }
+    }
+    // the sampler's own stream may be replaying iterations: order after them
+    if (s->own && cudaStreamSynchronize(s->own) != cudaSuccess) return HMM_ECUDA;
+    if (cudaMemcpyAsync(s->theta2, theta2, sizeof(float) * C * D, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return HMM_ECUDA;
+    // the second point's parameters, log prior, log likelihood, log posterior
+    // (the parameter buffers are scratch between iterations)
+    transform_kernel<<<C, TPB, smem_for(D), st>>>(K, D, s->theta2, s->prior, s->pi, s->P, s->p, s->mu, s->cov,
+                                                   s->logprior2);
+    if (cudaGetLastError() != cudaSuccess) return HMM_ECUDA;
+    int rc = hmm_loglik_batched(s->lik, C, K, s->pi, s->P, s->p, s->mu, s->cov, s->n_seg, s->offs, s->xy,
+                                s->tremor, &s->opts, s->loglik2, stream);
+    if (rc) return rc;
+    sum_kernel<<<(C + 127) / 128, 128, 0, st>>>(C, s->loglik2, s->logprior2, s->logpost2);
+    if (cudaGetLastError() != cudaSuccess) return HMM_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return HMM_ECUDA;
+    return hmm_sampler_set_proposal(s, HMM_PROPOSAL_TWALK, nullptr);
+}
+
+int hmm_sampler_twalk_state(hmm_sampler *s, float *theta2_out, double *logpost2_out, void *stream) {
+    if (!s || !s->theta2) return HMM_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (theta2_out)
+        e = cudaMemcpyAsync(theta2_out, s->theta2, sizeof(float) * s->C * s->D, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && logpost2_out)
+        e = cudaMemcpyAsync(logpost2_out, s->logpost2, sizeof(double) * s->C, cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? HMM_OK : HMM_ECUDA;
+}
+
 int hmm_sampler_set_proposal(hmm_sampler *s, int32_t kind, hmm_mlp *mlp) {
     if (!s) return HMM_EINVAL;
-    if (kind != HMM_PROPOSAL_RW && kind != HMM_PROPOSAL_MLP) return HMM_EINVAL;
+    if (kind != HMM_PROPOSAL_RW && kind != HMM_PROPOSAL_MLP && kind != HMM_PROPOSAL_TWALK) return HMM_EINVAL;
+    if (kind == HMM_PROPOSAL_TWALK && !s->theta2) return HMM_EINVAL;  // hmm_sampler_set_twalk first
     if (kind == HMM_PROPOSAL_MLP) {
         if (!mlp || mlp_dim(mlp) != s->D) return HMM_EINVAL;
         if (!s->mx) {
