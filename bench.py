@@ -15,10 +15,11 @@ Also reported on the same line:
                 the timed region);
   roofline      the chunk-product kernel against its peak;
   cpu_baseline  the FP64 CPU oracle on a bounded sample, on the host cores;
-  mcmc          effective samples per second of the log posterior, the
-                random-walk sampler against the learned (MLP) proposal trained
-                on the random walk's own history, same chains and iterations
-                (K=16, 512 chains; T reduced so the run stays within a minute).
+  mcmc          effective samples per second of the log posterior and of
+                label-invariant summaries: the random-walk sampler, the learned
+                (MLP) proposal trained on the random walk's own history, and
+                the t-walk, same chains and iterations (K=16, 512 chains; T
+                reduced so the run stays within about a minute).
 
 ``--impl reference`` times the CPU oracle instead (rank 0 only).
 Multi-GPU (torchrun): every rank evaluates its own n_prop proposals (weak

@@ -126,6 +126,7 @@ def rw_vs_learned(K=16, T=16384, chains=512, seed=0, burn=3000, history=200, lag
     rw.step(burn)
     _, hist, _ = _timed_run(rw, history, trace_theta=True)
     th_now, _, _, _ = rw.state()
+    th_early = hist[0].clone()  # each chain's state `history` iterations ago: the t-walk's second point
 
     t0 = time.perf_counter()
     ls = make(th_now, step, seed + 3)
@@ -148,6 +149,16 @@ def rw_vs_learned(K=16, T=16384, chains=512, seed=0, burn=3000, history=200, lag
     del th
     s_rw = _ess_summary(lp_rw, sm_rw, K)
     s_ml = _ess_summary(lp_ml, sm_ml, K)
+    # the t-walk (the paper's sampler) from the same states
+    tw = make(th_now, step, seed + 5)
+    tw.set_twalk(th_early)
+    na0 = tw.state()[3].clone()
+    lp_tw, th, t_tw = _timed_run(tw, n_measure, trace_theta=True)
+    acc_tw = float((tw.state()[3] - na0).double().mean().item()) / n_measure
+    sm_tw = invariant_summaries(th, K)
+    del th
+    s_tw = _ess_summary(lp_tw, sm_tw, K)
+    tw.close()
     e_rw, e_ml = s_rw["log_post"], s_ml["log_post"]
     finite = bool(torch.isfinite(lp_ml).all().item() and torch.isfinite(lp_rw).all().item())
     out = {
@@ -160,6 +171,9 @@ def rw_vs_learned(K=16, T=16384, chains=512, seed=0, burn=3000, history=200, lag
                     "ms_per_iter": 1e3 * t_ml / n_measure,
                     "ess_summaries_min": s_ml["summaries_min"], "ess_summaries_median": s_ml["summaries_median"],
                     "ess_per_s_training_amortised": e_ml / (t_ml + fit_s)},
+        "twalk": {"ess": s_tw["log_post"], "seconds": t_tw, "ess_per_s": s_tw["log_post"] / t_tw,
+                  "accept": acc_tw, "ms_per_iter": 1e3 * t_tw / n_measure,
+                  "ess_summaries_min": s_tw["summaries_min"], "ess_summaries_median": s_tw["summaries_median"]},
         "gain_ess_per_s": (e_ml / t_ml) / (e_rw / t_rw),
         "gain_ess_per_iter": e_ml / e_rw,
         "gain_summaries_min_per_s": (s_ml["summaries_min"] / t_ml) / (s_rw["summaries_min"] / t_rw),
