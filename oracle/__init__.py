@@ -83,6 +83,8 @@ def _declare_loglik(L):
                                         ctypes.c_int, _i64, _f, _u8, ctypes.c_int, _d,
                                         ctypes.c_int]
     L.oracle_loglik_batched.restype = None
+    L.oracle_posterior.argtypes = [ctypes.c_int, _f, _f, _f, _f, _f, ctypes.c_int64, _f, _u8, ctypes.c_int, _d]
+    L.oracle_posterior.restype = ctypes.c_double
 
 
 class OraclePrior(ctypes.Structure):
@@ -321,3 +323,12 @@ def twalk_gauss_run(x0, xp0, n_iter, seed, kernels=TWALK_MIXTURE, _L=None):
                                          x0.ctypes.data_as(_f),
                                  xp0.ctypes.data_as(_f), out.ctypes.data_as(_f), work.ctypes.data_as(_d))
     return out
+
+
+def posterior(prm, xy, tremor, init_mode: int = 0, _L=None):
+    """Posterior state probabilities gamma [T, K] (float64) and log L."""
+    keep, a = _args(_params(prm), xy, tremor)
+    K, T = a[0], a[6]
+    g = np.zeros((T, K), dtype=np.float64)
+    ll = (_L or lib()).oracle_posterior(*a, int(init_mode), g.ctypes.data_as(_d))
+    return g, float(ll)

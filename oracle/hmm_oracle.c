@@ -339,3 +339,75 @@ void oracle_loglik_batched(int n_prop, int K, const float *pi, const float *P,
     for (int i = 0; i < n_threads; ++i) pthread_join(th[i], NULL);
     pthread_mutex_destroy(&j.lock);
 }
+
+/*
+ * Posterior state probabilities gamma_t(k) = P(s_t = k | o_1..o_T), the
+ * smoothing step that follows the likelihood (the forward-backward
+ * algorithm; Rabiner, Proc. IEEE 1989, Section III-A). The forward
+ * vectors are normalised every step and stored in `gamma` (T x K); the
+ * backward recursion
+ *   b_T = 1,  b_t[i] = sum_j P_ij e_j(o_{t+1}) b_{t+1}[j]
+ * runs with its own per-step normalisation (any positive factor per step
+ * cancels), and gamma_t = alpha_t * b_t / sum_k alpha_t(k) b_t(k).
+ * Returns log L; for a zero likelihood gamma is set to NaN and -inf
+ * returned.
+ */
+double oracle_posterior(int K, const float *pi, const float *P, const float *p, const float *mu,
+                        const float *cov, int64_t T, const float *xy, const uint8_t *tremor, int init_mode,
+                        double *gamma)
+{
+    double *alpha = (double *)malloc(sizeof(double) * K);
+    double *beta = (double *)malloc(sizeof(double) * K);
+    double *nb = (double *)malloc(sizeof(double) * K);
+    double *le = (double *)malloc(sizeof(double) * K);
+    initial_vector(K, pi, P, init_mode, alpha);
+    double logL = 0.0;
+    int zero = 0;
+    for (int64_t t = 0; t < T && !zero; ++t) {
+        log_emissions(K, p, mu, cov, tremor[t], xy[2 * t], xy[2 * t + 1], le);
+        if (t == 0) {
+            for (int k = 0; k < K; ++k) beta[k] = alpha[k];
+        } else {
+            for (int j = 0; j < K; ++j) {
+                double s = 0.0;
+                for (int i = 0; i < K; ++i) s += alpha[i] * (double)P[i * K + j];
+                beta[j] = s;
+            }
+        }
+        double m = max_of(K, le), c = 0.0;
+        if (m == -INFINITY) { zero = 1; break; }
+        for (int k = 0; k < K; ++k) {
+            alpha[k] = beta[k] * exp(le[k] - m);
+            c += alpha[k];
+        }
+        if (!(c > 0.0)) { zero = 1; break; }
+        for (int k = 0; k < K; ++k) {
+            alpha[k] /= c;
+            gamma[t * K + k] = alpha[k];
+        }
+        logL += m + log(c);
+    }
+    if (zero) {
+        for (int64_t i = 0; i < T * K; ++i) gamma[i] = NAN;
+        free(alpha); free(beta); free(nb); free(le);
+        return -INFINITY;
+    }
+    for (int k = 0; k < K; ++k) beta[k] = 1.0;
+    for (int64_t t = T - 1; t >= 0; --t) {
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) s += gamma[t * K + k] * beta[k];
+        for (int k = 0; k < K; ++k) gamma[t * K + k] = gamma[t * K + k] * beta[k] / s;
+        if (t == 0) break;
+        log_emissions(K, p, mu, cov, tremor[t], xy[2 * t], xy[2 * t + 1], le);
+        double m = max_of(K, le), n = 0.0;
+        for (int i = 0; i < K; ++i) {
+            double v = 0.0;
+            for (int j = 0; j < K; ++j) v += (double)P[i * K + j] * exp(le[j] - m) * beta[j];
+            nb[i] = v;
+            if (v > n) n = v;
+        }
+        for (int i = 0; i < K; ++i) beta[i] = nb[i] / n;
+    }
+    free(alpha); free(beta); free(nb); free(le);
+    return logL;
+}
