@@ -115,6 +115,22 @@ const char *hmm_last_error(const hmm_ctx *ctx);
 int hmm_status(hmm_ctx *ctx, void *stream);
 
 /*
+ * Posterior state probabilities of one sequence: the smoothing step that
+ * follows the likelihood when tremor episodes are classified by hidden state
+ * (the forward-backward algorithm; Rabiner, Proc. IEEE 1989, Section III-A).
+ * gamma (device, T x K floats, row-major) receives
+ * gamma[t][k] = P(s_t = k | o_0 .. o_{T-1}); *loglik (device double)
+ * receives log L. Computed on the chunk structure of hmm_loglik, with the
+ * same options (opts->precision chooses the chunk products): two scans over
+ * the chunk products give the forward vector entering and the backward
+ * vector leaving every chunk, then every chunk recomputes its steps in FP32
+ * from both, normalising each vector every step. T >= 1. A zero likelihood
+ * gives NaN rows.
+ */
+int hmm_posterior(hmm_ctx *ctx, const hmm_params *params, const hmm_obs *obs, const hmm_opts *opts,
+                  float *gamma, double *loglik, void *stream);
+
+/*
  * log L for one parameter set and one sequence (Eq. "likelihood func",
  * computed as Section "The likelihood algorithm" restructures it).
  * out_dev: device pointer to one double.

@@ -85,6 +85,8 @@ SIGNATURES = {
     "hmm_status": (ctypes.c_int, [_VP, _VP]),
     "hmm_loglik": (ctypes.c_int, [_VP, ctypes.POINTER(hmm_params), ctypes.POINTER(hmm_obs),
                                   ctypes.POINTER(hmm_opts), _VP, _VP]),
+    "hmm_posterior": (ctypes.c_int, [_VP, ctypes.POINTER(hmm_params), ctypes.POINTER(hmm_obs),
+                                     ctypes.POINTER(hmm_opts), _VP, _VP, _VP]),
     "hmm_loglik_batched": (ctypes.c_int, [_VP, _I32, _I32, _VP, _VP, _VP, _VP, _VP, _I32, _VP,
                                           _VP, _VP, ctypes.POINTER(hmm_opts), _VP, _VP]),
     "hmm_loglik_batched_host": (ctypes.c_int, [_VP, _I32, _I32, _VP, _VP, _VP, _VP, _VP, _I32,
@@ -222,6 +224,23 @@ class Context:
     def hmm_status(self, stream=None) -> int:
         """Synchronise, read and clear the device status word (returns the code)."""
         return int(self.lib.hmm_status(self.h, _stream_ptr(stream)))
+
+    def hmm_posterior(self, pi, P, p_tremor, mu, cov, xy, tremor, opts=None, stream=None):
+        """Posterior state probabilities [T, K] (float32) and log L (float64 [1]) of one sequence."""
+        K = int(pi.shape[0])
+        for t, n in ((pi, "pi"), (P, "P"), (p_tremor, "p_tremor"), (mu, "mu"), (cov, "cov")):
+            _dev(t, torch.float32, n)
+        _dev(xy, torch.float32, "xy")
+        _dev(tremor, torch.uint8, "tremor")
+        T = int(tremor.shape[0])
+        gamma = torch.empty(T, K, dtype=torch.float32, device=pi.device)
+        ll = torch.empty(1, dtype=torch.float64, device=pi.device)
+        prm = hmm_params(K, pi.data_ptr(), P.data_ptr(), p_tremor.data_ptr(), mu.data_ptr(), cov.data_ptr())
+        ob = hmm_obs(T, xy.data_ptr() if T else None, tremor.data_ptr() if T else None)
+        o = opts if opts is not None else make_opts()
+        self._check(self.lib.hmm_posterior(self.h, ctypes.byref(prm), ctypes.byref(ob), ctypes.byref(o),
+                                           gamma.data_ptr(), ll.data_ptr(), _stream_ptr(stream)))
+        return gamma, ll
 
     def hmm_loglik(self, pi, P, p_tremor, mu, cov, xy, tremor, opts=None, out=None, stream=None):
         """log L of one parameter set on one sequence; returns a float64 [1] CUDA tensor."""

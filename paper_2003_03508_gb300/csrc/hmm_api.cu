@@ -58,6 +58,7 @@ struct hmm_ctx {
     DevBuf work;       // per-call workspace
     DevBuf planbuf;    // plan tables
     DevBuf stage;      // staging area for the _host entry point
+    DevBuf fb;         // boundary vectors of hmm_posterior
     unsigned *d_status = nullptr;
     Plan plan;
     int last_launches = 0;
@@ -380,6 +381,32 @@ int hmm_status(hmm_ctx *c, void *stream) {
     return HMM_OK;
 }
 
+// The per-call workspace, in carving order (sizes only when base is null).
+struct WorkPtrs {
+    float *cblock = nullptr;
+    int *prop_bad = nullptr, *obs_bad = nullptr;
+    float2 *packed = nullptr, *head = nullptr;
+    LevelPtrs lv{};
+};
+
+static size_t carve_work(void *base, int n_prop, int n_seg, const ConstLayout &lay, const Plan &pl, WorkPtrs *w) {
+    const int KP = lay.KP;
+    Carve cv(base);
+    w->cblock = cv.take<float>((size_t)n_prop * lay.stride);
+    w->prop_bad = cv.take<int>(n_prop);
+    w->obs_bad = cv.take<int>(1);
+    w->packed = cv.take<float2>(pl.n_packed);
+    w->head = cv.take<float2>(n_seg);
+    w->lv = LevelPtrs{};
+    for (int l = 0; l <= pl.n_levels; ++l) {
+        w->lv.A[l] = cv.take<float>((size_t)n_prop * std::max(1, pl.level_n[l]) * KP * KP);
+        if (l == 0) w->lv.e[l] = cv.take<int32_t>((size_t)n_prop * std::max(1, pl.level_n[l]) * KP);
+        else w->lv.e[l] = cv.take<long long>((size_t)n_prop * std::max(1, pl.level_n[l]) * KP);
+        w->lv.n[l] = pl.level_n[l];
+    }
+    return cv.off;
+}
+
 int hmm_loglik_batched(hmm_ctx *c, int32_t n_prop, int32_t K, const float *pi, const float *P,
                        const float *p, const float *mu, const float *cov, int32_t n_seg,
                        const int64_t *offs, const float *xy, const uint8_t *tremor,
@@ -437,32 +464,16 @@ int hmm_loglik_batched(hmm_ctx *c, int32_t n_prop, int32_t K, const float *pi, c
 
     // ---- workspace ----
     const int KP = lay.KP;
-    size_t need = 0;
-    auto add = [&](size_t b) { need += (b + 255) & ~(size_t)255; };
-    add(sizeof(float) * (size_t)n_prop * lay.stride);
-    add(sizeof(int) * (size_t)n_prop);
-    add(sizeof(int));
-    add(sizeof(float2) * (size_t)pl.n_packed);
-    add(sizeof(float2) * (size_t)n_seg);
-    for (int l = 0; l <= pl.n_levels; ++l) {
-        add(sizeof(float) * (size_t)n_prop * std::max(1, pl.level_n[l]) * KP * KP);
-        add((l == 0 ? 4 : 8) * (size_t)n_prop * std::max(1, pl.level_n[l]) * KP);
-    }
-    int rc = ensure(c, c->work, need + 4096);
+    WorkPtrs wp;
+    int rc = ensure(c, c->work, carve_work(nullptr, n_prop, n_seg, lay, pl, &wp) + 4096);
     if (rc) return rc;
-    Carve cv(c->work.p);
-    float *cblock = cv.take<float>((size_t)n_prop * lay.stride);
-    int *prop_bad = cv.take<int>(n_prop);
-    int *obs_bad = cv.take<int>(1);
-    float2 *packed = cv.take<float2>(pl.n_packed);
-    float2 *head = cv.take<float2>(n_seg);
-    LevelPtrs lv{};
-    for (int l = 0; l <= pl.n_levels; ++l) {
-        lv.A[l] = cv.take<float>((size_t)n_prop * std::max(1, pl.level_n[l]) * KP * KP);
-        if (l == 0) lv.e[l] = cv.take<int32_t>((size_t)n_prop * std::max(1, pl.level_n[l]) * KP);
-        else lv.e[l] = cv.take<long long>((size_t)n_prop * std::max(1, pl.level_n[l]) * KP);
-        lv.n[l] = pl.level_n[l];
-    }
+    carve_work(c->work.p, n_prop, n_seg, lay, pl, &wp);
+    float *cblock = wp.cblock;
+    int *prop_bad = wp.prop_bad;
+    int *obs_bad = wp.obs_bad;
+    float2 *packed = wp.packed;
+    float2 *head = wp.head;
+    LevelPtrs lv = wp.lv;
 
     // ---- launches ----
     int launches = 0;
@@ -505,6 +516,39 @@ int hmm_loglik(hmm_ctx *c, const hmm_params *prm, const hmm_obs *obs, const hmm_
     int64_t offs[2] = {0, obs->T};
     return hmm_loglik_batched(c, 1, prm->K, prm->pi, prm->P, prm->p_tremor, prm->mu, prm->cov, 1,
                               offs, obs->xy, obs->tremor, opts, out, stream);
+}
+
+int hmm_posterior(hmm_ctx *c, const hmm_params *prm, const hmm_obs *obs, const hmm_opts *opts, float *gamma,
+                  double *loglik, void *stream) {
+    if (!c) return HMM_EINVAL;
+    if (!prm || !obs || !gamma || !loglik) return fail(c, HMM_EINVAL, "null argument");
+    if (obs->T < 1) return fail(c, HMM_EINVAL, "T must be >= 1");
+    int64_t offs[2] = {0, obs->T};
+    hmm_opts o;
+    if (opts) o = *opts; else hmm_opts_default(&o);
+    if (o.chunk_len == 0) {
+        // the boundary scans cost ~1.5 us per chunk in sequence and every chunk
+        // ~0.5 us per step (all chunks in one wave): L ~ sqrt(3 T) balances them
+        const int64_t Lp = ((int64_t)std::sqrt(3.0 * (double)obs->T) + OBS_WIN - 1) / OBS_WIN * OBS_WIN;
+        o.chunk_len = (int32_t)std::min<int64_t>(16384, std::max<int64_t>(OBS_WIN, Lp));
+    }
+    // the likelihood path computes the chunk products (and log L)
+    int rc = hmm_loglik_batched(c, 1, prm->K, prm->pi, prm->P, prm->p_tremor, prm->mu, prm->cov, 1, offs, obs->xy,
+                                obs->tremor, &o, loglik, stream);
+    if (rc) return rc;
+    const Plan &pl = c->plan;
+    WorkPtrs wp;
+    carve_work(c->work.p, 1, 1, pl.lay, pl, &wp);
+    rc = ensure(c, c->fb, sizeof(float) * 2 * (size_t)std::max(1, pl.n_chunks) * pl.lay.KP + 256);
+    if (rc) return rc;
+    float *fvec = (float *)c->fb.p;
+    float *bvec = fvec + (size_t)std::max(1, pl.n_chunks) * pl.lay.KP;
+    cudaError_t e = launch_posterior(prm->K, pl.lay.KP, o.init_mode, pl.n_chunks, pl.L, pl.d_chunks, prm->pi, prm->P,
+                                     wp.cblock + pl.lay.off_emis, wp.head, wp.packed, wp.lv.A[0],
+                                     (const int32_t *)wp.lv.e[0], fvec, bvec, gamma, (cudaStream_t)stream);
+    c->last_launches += 1 + (pl.n_chunks > 0 ? 1 : 0);
+    if (e != cudaSuccess) return cuda_fail(c, e, "posterior launch");
+    return HMM_OK;
 }
 
 int hmm_loglik_batched_host(hmm_ctx *c, int32_t n_prop, int32_t K, const float *pi, const float *P,
