@@ -85,6 +85,9 @@ def _declare_loglik(L):
     L.oracle_loglik_batched.restype = None
     L.oracle_posterior.argtypes = [ctypes.c_int, _f, _f, _f, _f, _f, ctypes.c_int64, _f, _u8, ctypes.c_int, _d]
     L.oracle_posterior.restype = ctypes.c_double
+    L.oracle_expected_stats.argtypes = [ctypes.c_int, _f, _f, _f, _f, _f, ctypes.c_int64, _f, _u8, ctypes.c_int,
+                                        _d]
+    L.oracle_expected_stats.restype = ctypes.c_double
 
 
 class OraclePrior(ctypes.Structure):
@@ -332,3 +335,24 @@ def posterior(prm, xy, tremor, init_mode: int = 0, _L=None):
     g = np.zeros((T, K), dtype=np.float64)
     ll = (_L or lib()).oracle_posterior(*a, int(init_mode), g.ctypes.data_as(_d))
     return g, float(ll)
+
+
+STAT_NAMES = ("N", "G0", "Gs", "Gr", "Sx", "Sy", "Sxx", "Sxy", "Syy")
+
+
+def split_stats(flat, K):
+    """The flat statistics vector (K*K + 8K) as a dict of arrays."""
+    flat = np.asarray(flat)
+    out = {"N": flat[:K * K].reshape(K, K)}
+    for i, name in enumerate(STAT_NAMES[1:]):
+        out[name] = flat[K * K + i * K:K * K + (i + 1) * K]
+    return out
+
+
+def expected_stats(prm, xy, tremor, init_mode: int = 0, _L=None):
+    """E-step statistics (dict, float64) and log L (hmm_oracle.c)."""
+    keep, a = _args(_params(prm), xy, tremor)
+    K = a[0]
+    st = np.zeros(K * K + 8 * K, dtype=np.float64)
+    ll = (_L or lib()).oracle_expected_stats(*a, int(init_mode), st.ctypes.data_as(_d))
+    return split_stats(st, K), float(ll)

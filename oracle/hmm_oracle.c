@@ -411,3 +411,98 @@ double oracle_posterior(int K, const float *pi, const float *P, const float *p, 
     free(alpha); free(beta); free(nb); free(le);
     return logL;
 }
+
+/*
+ * Expected sufficient statistics of the hidden chain given the observations
+ * (the E-step of EM, Baum-Welch; Rabiner 1989, Section III-C), written to
+ * `stats` (K*K + 8*K doubles, in this order):
+ *   N[i][j] = sum_{t>=1} P(s_{t-1}=i, s_t=j | o)   expected transitions
+ *   G0[k]   = P(s_0 = k | o)
+ *   Gs[k]   = sum_t gamma_t(k)
+ *   Gr[k]   = sum_t gamma_t(k) [tremor at t]
+ *   Sx[k], Sy[k]            = sum_t gamma_t(k) [tremor] x_t, y_t
+ *   Sxx[k], Sxy[k], Syy[k]  = sum_t gamma_t(k) [tremor] x_t^2, x_t y_t, y_t^2
+ * With the Fisher identity (the gradient of log L is the posterior
+ * expectation of the gradient of the complete-data log likelihood) these
+ * give d log L / d(pi, P, p, mu, Sigma). Returns log L.
+ */
+double oracle_expected_stats(int K, const float *pi, const float *P, const float *p, const float *mu,
+                             const float *cov, int64_t T, const float *xy, const uint8_t *tremor, int init_mode,
+                             double *stats)
+{
+    double *gam = (double *)malloc(sizeof(double) * (size_t)(T > 0 ? T : 1) * K);
+    double *fwd = (double *)malloc(sizeof(double) * (size_t)(T > 0 ? T : 1) * K);
+    double *beta = (double *)malloc(sizeof(double) * K);
+    double *nb = (double *)malloc(sizeof(double) * K);
+    double *le = (double *)malloc(sizeof(double) * K);
+    double *w = (double *)malloc(sizeof(double) * K);
+    double *N = stats, *G0 = stats + K * K, *Gs = G0 + K, *Gr = Gs + K, *Sx = Gr + K, *Sy = Sx + K;
+    double *Sxx = Sy + K, *Sxy = Sxx + K, *Syy = Sxy + K;
+    memset(stats, 0, sizeof(double) * (size_t)(K * K + 8 * K));
+    /* forward vectors (normalised) via the posterior routine's recursion */
+    double logL = oracle_posterior(K, pi, P, p, mu, cov, T, xy, tremor, init_mode, gam);
+    if (!(logL > -INFINITY) || T == 0) {
+        free(gam); free(fwd); free(beta); free(nb); free(le); free(w);
+        return logL;
+    }
+    /* forward vectors again, kept for the pairwise terms */
+    {
+        double *a = (double *)malloc(sizeof(double) * K);
+        initial_vector(K, pi, P, init_mode, a);
+        for (int64_t t = 0; t < T; ++t) {
+            log_emissions(K, p, mu, cov, tremor[t], xy[2 * t], xy[2 * t + 1], le);
+            double m = max_of(K, le), c = 0.0;
+            for (int j = 0; j < K; ++j) {
+                double s;
+                if (t == 0) {
+                    s = a[j];
+                } else {
+                    s = 0.0;
+                    for (int i = 0; i < K; ++i) s += fwd[(t - 1) * K + i] * (double)P[i * K + j];
+                }
+                w[j] = s * exp(le[j] - m);
+                c += w[j];
+            }
+            for (int j = 0; j < K; ++j) fwd[t * K + j] = w[j] / c;
+        }
+        free(a);
+    }
+    /* backward pass: pairwise posteriors xi_t(i,j) ∝ f_{t-1}(i) P_ij e_j(o_t) b_t(j) */
+    for (int k = 0; k < K; ++k) beta[k] = 1.0;
+    for (int64_t t = T - 1; t >= 1; --t) {
+        log_emissions(K, p, mu, cov, tremor[t], xy[2 * t], xy[2 * t + 1], le);
+        double m = max_of(K, le), z = 0.0;
+        for (int j = 0; j < K; ++j) w[j] = exp(le[j] - m) * beta[j];
+        for (int i = 0; i < K; ++i)
+            for (int j = 0; j < K; ++j) z += fwd[(t - 1) * K + i] * (double)P[i * K + j] * w[j];
+        for (int i = 0; i < K; ++i)
+            for (int j = 0; j < K; ++j) N[i * K + j] += fwd[(t - 1) * K + i] * (double)P[i * K + j] * w[j] / z;
+        double n = 0.0;
+        for (int i = 0; i < K; ++i) {
+            double v = 0.0;
+            for (int j = 0; j < K; ++j) v += (double)P[i * K + j] * w[j];
+            nb[i] = v;
+            if (v > n) n = v;
+        }
+        for (int i = 0; i < K; ++i) beta[i] = nb[i] / n;
+    }
+    for (int64_t t = 0; t < T; ++t) {
+        const int tr = tremor[t] != 0;
+        const double x = xy[2 * t], y = xy[2 * t + 1];
+        for (int k = 0; k < K; ++k) {
+            const double g = gam[t * K + k];
+            if (t == 0) G0[k] = g;
+            Gs[k] += g;
+            if (tr) {
+                Gr[k] += g;
+                Sx[k] += g * x;
+                Sy[k] += g * y;
+                Sxx[k] += g * x * x;
+                Sxy[k] += g * x * y;
+                Syy[k] += g * y * y;
+            }
+        }
+    }
+    free(gam); free(fwd); free(beta); free(nb); free(le); free(w);
+    return logL;
+}
