@@ -131,6 +131,22 @@ int hmm_posterior(hmm_ctx *ctx, const hmm_params *params, const hmm_obs *obs, co
                   float *gamma, double *loglik, void *stream);
 
 /*
+ * Expected sufficient statistics of the hidden chain (the E-step of EM,
+ * Baum-Welch; Rabiner 1989, Section III-C), from the same chunked forward-
+ * backward pass as hmm_posterior, into `stats` (device, K*K + 8*K doubles):
+ *   N[i][j] = sum_{t>=1} P(s_{t-1}=i, s_t=j | o)  (K*K, row-major)
+ *   G0[k] = P(s_0 = k | o); Gs[k] = sum_t gamma_t(k);
+ *   Gr[k] = sum over tremor steps of gamma_t(k);
+ *   Sx, Sy, Sxx, Sxy, Syy [k] = the same sums weighted by x, y, x^2, xy, y^2
+ * (K each, in this order after N). With the Fisher identity they give the
+ * gradient of log L with respect to every parameter (for gradient-based
+ * samplers), and an EM update. Chunk partial sums are added in chunk order
+ * in FP64 (deterministic). *loglik (device) receives log L. T >= 2.
+ */
+int hmm_expected_stats(hmm_ctx *ctx, const hmm_params *params, const hmm_obs *obs, const hmm_opts *opts,
+                       double *stats, double *loglik, void *stream);
+
+/*
  * log L for one parameter set and one sequence (Eq. "likelihood func",
  * computed as Section "The likelihood algorithm" restructures it).
  * out_dev: device pointer to one double.

@@ -58,7 +58,8 @@ struct hmm_ctx {
     DevBuf work;       // per-call workspace
     DevBuf planbuf;    // plan tables
     DevBuf stage;      // staging area for the _host entry point
-    DevBuf fb;         // boundary vectors of hmm_posterior
+    DevBuf fb;         // boundary vectors (and partial statistics) of hmm_posterior
+    DevBuf gam;        // posterior vectors of hmm_expected_stats
     unsigned *d_status = nullptr;
     Plan plan;
     int last_launches = 0;
@@ -518,8 +519,9 @@ int hmm_loglik(hmm_ctx *c, const hmm_params *prm, const hmm_obs *obs, const hmm_
                               offs, obs->xy, obs->tremor, opts, out, stream);
 }
 
-int hmm_posterior(hmm_ctx *c, const hmm_params *prm, const hmm_obs *obs, const hmm_opts *opts, float *gamma,
-                  double *loglik, void *stream) {
+// the posterior (and optionally the E-step statistics) of one sequence
+static int posterior_impl(hmm_ctx *c, const hmm_params *prm, const hmm_obs *obs, const hmm_opts *opts,
+                          float *gamma, double *loglik, double *stats, void *stream) {
     if (!c) return HMM_EINVAL;
     if (!prm || !obs || !gamma || !loglik) return fail(c, HMM_EINVAL, "null argument");
     if (obs->T < 1) return fail(c, HMM_EINVAL, "T must be >= 1");
@@ -537,18 +539,43 @@ int hmm_posterior(hmm_ctx *c, const hmm_params *prm, const hmm_obs *obs, const h
                                 obs->tremor, &o, loglik, stream);
     if (rc) return rc;
     const Plan &pl = c->plan;
+    const int K = prm->K, KP = pl.lay.KP, C = std::max(1, pl.n_chunks);
     WorkPtrs wp;
     carve_work(c->work.p, 1, 1, pl.lay, pl, &wp);
-    rc = ensure(c, c->fb, sizeof(float) * 2 * (size_t)std::max(1, pl.n_chunks) * pl.lay.KP + 256);
+    size_t fb_bytes = sizeof(float) * 2 * (size_t)C * KP + 256;
+    if (stats) fb_bytes += sizeof(double) * ((size_t)C * (K * K + 7 * K) + K) + 256;
+    rc = ensure(c, c->fb, fb_bytes);
     if (rc) return rc;
     float *fvec = (float *)c->fb.p;
-    float *bvec = fvec + (size_t)std::max(1, pl.n_chunks) * pl.lay.KP;
-    cudaError_t e = launch_posterior(prm->K, pl.lay.KP, o.init_mode, pl.n_chunks, pl.L, pl.d_chunks, prm->pi, prm->P,
+    float *bvec = fvec + (size_t)C * KP;
+    double *part = nullptr, *g0 = nullptr;
+    if (stats) {
+        part = (double *)(((uintptr_t)(bvec + (size_t)C * KP) + 255) & ~(uintptr_t)255);
+        g0 = part + (size_t)C * (K * K + 7 * K);
+    }
+    cudaError_t e = launch_posterior(K, KP, o.init_mode, pl.n_chunks, pl.L, pl.d_chunks, prm->pi, prm->P,
                                      wp.cblock + pl.lay.off_emis, wp.head, wp.packed, wp.lv.A[0],
-                                     (const int32_t *)wp.lv.e[0], fvec, bvec, gamma, (cudaStream_t)stream);
-    c->last_launches += 1 + (pl.n_chunks > 0 ? 1 : 0);
+                                     (const int32_t *)wp.lv.e[0], fvec, bvec, gamma, part, g0, stats,
+                                     (cudaStream_t)stream);
+    c->last_launches += 1 + (pl.n_chunks > 0 ? 1 : 0) + (stats && pl.n_chunks > 0 ? 1 : 0);
     if (e != cudaSuccess) return cuda_fail(c, e, "posterior launch");
     return HMM_OK;
+}
+
+int hmm_posterior(hmm_ctx *c, const hmm_params *prm, const hmm_obs *obs, const hmm_opts *opts, float *gamma,
+                  double *loglik, void *stream) {
+    return posterior_impl(c, prm, obs, opts, gamma, loglik, nullptr, stream);
+}
+
+int hmm_expected_stats(hmm_ctx *c, const hmm_params *prm, const hmm_obs *obs, const hmm_opts *opts,
+                       double *stats, double *loglik, void *stream) {
+    if (!c) return HMM_EINVAL;
+    if (!prm || !obs || !stats || !loglik) return fail(c, HMM_EINVAL, "null argument");
+    if (obs->T < 2) return fail(c, HMM_EINVAL, "T must be >= 2");
+    // the posterior vectors go to a context-owned buffer
+    int rc = ensure(c, c->gam, sizeof(float) * (size_t)obs->T * prm->K + 256);
+    if (rc) return rc;
+    return posterior_impl(c, prm, obs, opts, (float *)c->gam.p, loglik, stats, stream);
 }
 
 int hmm_loglik_batched_host(hmm_ctx *c, int32_t n_prop, int32_t K, const float *pi, const float *P,

@@ -138,7 +138,7 @@ int chunk_tc_chunks_per_item(int KP, int precision);
 cudaError_t launch_posterior(int K, int KP, int init_mode, int n_chunks, int L, const ChunkDesc *chunks,
                              const float *pi, const float *P, const float *em, const float2 *head,
                              const float2 *packed, const float *A0, const int32_t *e0, float *fvec, float *bvec,
-                             float *gamma, cudaStream_t st);
+                             float *gamma, double *stats_part, double *g0, double *stats, cudaStream_t st);
 int chunk_tc_wide_chunks_per_item(int KP, int precision);
 cudaError_t launch_chunk_tc_wide(int n_prop, int n_chunks, int renorm, int precision, const ConstLayout &lay,
                                  const float *cblock, const ChunkDesc *chunks, const float2 *packed, float *A0,

@@ -12,6 +12,13 @@
 //      (storing them in the output), and runs the backward recursion from b_c,
 //      turning each stored alpha_t into gamma_t = alpha_t o b_t / sum.
 // Each vector is normalised every step; gamma needs no absolute scale.
+//
+// With a statistics buffer, the backward pass also accumulates the E-step
+// statistics of the chunk (Baum-Welch): the pairwise posteriors
+// xi_t(i, j) ∝ alpha_{t-1}(i) P_ij e_j(o_t) b_t(j) summed into expected
+// transition counts, and the gamma-weighted tremor counts and location
+// moments; a second kernel adds the chunks' partial sums in chunk order in
+// FP64, so the result does not depend on scheduling.
 #include "hmm_internal.cuh"
 
 namespace hmm {
@@ -127,9 +134,26 @@ __global__ void __launch_bounds__(FB_THREADS) fb_scan_kernel(int K, int KP, int 
     }
 }
 
+// per-chunk partial statistics: N (K x K), then Gs, Gr, Sx, Sy, Sxx, Sxy, Syy (K each)
+constexpr int N_MOM = 7;
+
+__device__ void add_gamma_moments(double *acc, float g, float2 o) {
+    acc[0] += g;
+    if (!isnan(o.x)) {
+        const double x = o.x, y = o.y;
+        acc[1] += g;
+        acc[2] += g * x;
+        acc[3] += g * y;
+        acc[4] += g * x * x;
+        acc[5] += g * x * y;
+        acc[6] += g * y * y;
+    }
+}
+
 // One CTA per chunk: forward vectors from fvec[c] (stored in gamma), then the
-// backward recursion from bvec[c] turning them into posterior probabilities;
-// chunk 0 also writes gamma_0 from the head vector.
+// backward recursion from bvec[c] turning them into posterior probabilities
+// (and, with stats_part, the chunk's E-step statistics); chunk 0 also writes
+// gamma_0 from the head vector.
 __global__ void __launch_bounds__(FB_THREADS) fb_chunk_kernel(int K, int KP, int init_mode, int L,
                                                               const ChunkDesc *__restrict__ chunks,
                                                               const float *__restrict__ pi, const float *__restrict__ P,
@@ -137,18 +161,23 @@ __global__ void __launch_bounds__(FB_THREADS) fb_chunk_kernel(int K, int KP, int
                                                               const float2 *__restrict__ head,
                                                               const float2 *__restrict__ packed,
                                                               const float *__restrict__ fvec,
-                                                              const float *__restrict__ bvec, float *gamma) {
-    extern __shared__ float sP[];            // K x K (row-major), then its transpose
-    float *sPT = sP + K * K;
-    float *vec = sPT + K * K;                // K
-    float *red = vec + KP;                   // FB_THREADS / 32
+                                                              const float *__restrict__ bvec, float *gamma,
+                                                              double *stats_part, double *g0) {
+    extern __shared__ double sN[];           // K x K expected transitions (with statistics, FP64)
+    float *sP = reinterpret_cast<float *>(sN + (stats_part ? K * K : 0));  // K x K (row-major)
+    float *sPT = sP + K * K;                 // its transpose
+    float *vec = sPT + K * K;                // KP
+    float *aprev = vec + KP;                 // KP
+    float *red = aprev + KP;                 // FB_THREADS / 32
     const int c = blockIdx.x;
     const int j = threadIdx.x;
     for (int idx = j; idx < K * K; idx += FB_THREADS) {
         const float v = P[idx];
         sP[idx] = v;
         sPT[(idx % K) * K + idx / K] = v;
+        if (stats_part) sN[idx] = 0.0;
     }
+    double mom[N_MOM] = {0, 0, 0, 0, 0, 0, 0};
     const ChunkDesc cd = chunks[c];
     const int64_t t0 = (int64_t)c * L + 1;  // observation index of the chunk's first step (one segment)
     float a = j < K ? fvec[(size_t)c * KP + j] : 0.0f;
@@ -174,12 +203,27 @@ __global__ void __launch_bounds__(FB_THREADS) fb_chunk_kernel(int K, int KP, int
         const int64_t t = t0 + s;
         const float g = j < K ? gamma[(size_t)t * K + j] * b : 0.0f;
         const float sum = block_reduce(g, red, false);
-        if (j < K) gamma[(size_t)t * K + j] = sum > 0.0f ? g / sum : __int_as_float(0x7fc00000);
+        const float gn = sum > 0.0f ? g / sum : __int_as_float(0x7fc00000);
+        if (j < K) gamma[(size_t)t * K + j] = gn;
         const float2 o = packed[cd.pstart + s];
+        if (stats_part && j < K) add_gamma_moments(mom, gn, o);
         const float l = j < K ? log2_emission(em, KP, j, o.x, o.y, !isnan(o.x)) : -INFINITY;
         const float m = block_reduce(l, red, true);
         if (j < KP) vec[j] = (j < K && m > -INFINITY) ? exp2f(l - m) * b : 0.0f;
+        if (stats_part && j < KP)
+            aprev[j] = j < K ? (s > 0 ? gamma[(size_t)(t - 1) * K + j] : fvec[(size_t)c * KP + j]) : 0.0f;
         __syncthreads();
+        if (stats_part) {
+            // xi_t(i, j) = aprev_i P_ij vec_j / Z, Z = sum_j (aprev P)_j vec_j
+            float colj = 0.0f;
+            if (j < K)
+                for (int i = 0; i < K; ++i) colj = fmaf(aprev[i], sP[i * K + j], colj);
+            const float Z = block_reduce(j < K ? colj * vec[j] : 0.0f, red, false);
+            if (j < K && Z > 0.0f) {
+                const float u = vec[j] / Z;
+                for (int i = 0; i < K; ++i) sN[i * K + j] += (double)(aprev[i] * sP[i * K + j] * u);
+            }
+        }
         float w = 0.0f;
         if (j < K)
             for (int k = 0; k < K; ++k) w = fmaf(sPT[k * K + j], vec[k], w);
@@ -190,8 +234,34 @@ __global__ void __launch_bounds__(FB_THREADS) fb_chunk_kernel(int K, int KP, int
         const float h = head_vector(K, KP, init_mode, pi, P, em, head[0], red);
         const float g = j < K ? h * b : 0.0f;
         const float sum = block_reduce(g, red, false);
-        if (j < K) gamma[j] = sum > 0.0f ? g / sum : __int_as_float(0x7fc00000);
+        const float gn = sum > 0.0f ? g / sum : __int_as_float(0x7fc00000);
+        if (j < K) gamma[j] = gn;
+        if (stats_part && j < K) {
+            add_gamma_moments(mom, gn, head[0]);
+            g0[j] = gn;
+        }
     }
+    if (stats_part) {
+        __syncthreads();
+        double *dst = stats_part + (size_t)c * (K * K + N_MOM * K);
+        for (int idx = j; idx < K * K; idx += FB_THREADS) dst[idx] = sN[idx];
+        if (j < K)
+            for (int r = 0; r < N_MOM; ++r) dst[K * K + r * K + j] = mom[r];
+    }
+}
+
+// stats = [N (K x K), G0, Gs, Gr, Sx, Sy, Sxx, Sxy, Syy]: the chunks'
+// partial sums added in chunk order (one thread per entry)
+__global__ void fb_stats_reduce_kernel(int K, int n_chunks, const double *__restrict__ part,
+                                       const double *__restrict__ g0, double *stats) {
+    const int n = K * K + N_MOM * K;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int c = 0; c < n_chunks; ++c) acc += part[(size_t)c * n + e];
+        // G0 sits between N and the moments
+        stats[e < K * K ? e : e + K] = acc;
+    }
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) stats[K * K + k] = g0[k];
 }
 
 }  // namespace
@@ -199,9 +269,10 @@ __global__ void __launch_bounds__(FB_THREADS) fb_chunk_kernel(int K, int KP, int
 cudaError_t launch_posterior(int K, int KP, int init_mode, int n_chunks, int L, const ChunkDesc *chunks,
                              const float *pi, const float *P, const float *em, const float2 *head,
                              const float2 *packed, const float *A0, const int32_t *e0, float *fvec, float *bvec,
-                             float *gamma, cudaStream_t st) {
+                             float *gamma, double *stats_part, double *g0, double *stats, cudaStream_t st) {
     const size_t scan_smem = sizeof(float) * ((size_t)KP * KP + KP + FB_THREADS / 32) + sizeof(int) * FB_THREADS / 32;
-    const size_t chunk_smem = sizeof(float) * (2 * (size_t)K * K + KP + FB_THREADS / 32);
+    const size_t chunk_smem = (stats_part ? sizeof(double) * (size_t)K * K : 0) +
+                              sizeof(float) * (2 * (size_t)K * K + 2 * KP + FB_THREADS / 32);
     cudaError_t e = cudaFuncSetAttribute(fb_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scan_smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(fb_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chunk_smem);
@@ -210,7 +281,9 @@ cudaError_t launch_posterior(int K, int KP, int init_mode, int n_chunks, int L, 
                                                       bvec, gamma);
     if (n_chunks > 0)
         fb_chunk_kernel<<<n_chunks, FB_THREADS, chunk_smem, st>>>(K, KP, init_mode, L, chunks, pi, P, em, head,
-                                                                   packed, fvec, bvec, gamma);
+                                                                   packed, fvec, bvec, gamma, stats_part, g0);
+    if (stats && n_chunks > 0)
+        fb_stats_reduce_kernel<<<(K * K + N_MOM * K + 255) / 256, 256, 0, st>>>(K, n_chunks, stats_part, g0, stats);
     return cudaGetLastError();
 }
 
