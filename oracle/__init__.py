@@ -88,6 +88,11 @@ def _declare_loglik(L):
     L.oracle_expected_stats.argtypes = [ctypes.c_int, _f, _f, _f, _f, _f, ctypes.c_int64, _f, _u8, ctypes.c_int,
                                         _d]
     L.oracle_expected_stats.restype = ctypes.c_double
+    L.oracle_viterbi.argtypes = [ctypes.c_int, _f, _f, _f, _f, _f, ctypes.c_int64, _f, _u8, ctypes.c_int, _i32]
+    L.oracle_viterbi.restype = ctypes.c_double
+    L.oracle_path_logjoint.argtypes = [ctypes.c_int, _f, _f, _f, _f, _f, ctypes.c_int64, _f, _u8, ctypes.c_int,
+                                       _i32]
+    L.oracle_path_logjoint.restype = ctypes.c_double
 
 
 class OraclePrior(ctypes.Structure):
@@ -356,3 +361,19 @@ def expected_stats(prm, xy, tremor, init_mode: int = 0, _L=None):
     st = np.zeros(K * K + 8 * K, dtype=np.float64)
     ll = (_L or lib()).oracle_expected_stats(*a, int(init_mode), st.ctypes.data_as(_d))
     return split_stats(st, K), float(ll)
+
+
+def viterbi(prm, xy, tremor, init_mode: int = 0, _L=None):
+    """Most probable hidden path (int32 [T]) and its log joint probability."""
+    keep, a = _args(_params(prm), xy, tremor)
+    T = a[6]
+    path = np.zeros(max(T, 1), dtype=np.int32)
+    v = (_L or lib()).oracle_viterbi(*a, int(init_mode), path.ctypes.data_as(_i32))
+    return path[:T], float(v)
+
+
+def path_logjoint(prm, xy, tremor, path, init_mode: int = 0):
+    """log p(path, observations)."""
+    keep, a = _args(_params(prm), xy, tremor)
+    path = np.ascontiguousarray(np.asarray(path, dtype=np.int32))
+    return float(lib().oracle_path_logjoint(*a, int(init_mode), path.ctypes.data_as(_i32)))

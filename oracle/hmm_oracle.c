@@ -506,3 +506,66 @@ double oracle_expected_stats(int K, const float *pi, const float *P, const float
     free(gam); free(fwd); free(beta); free(nb); free(le); free(w);
     return logL;
 }
+
+/*
+ * The most probable hidden path (Viterbi; Rabiner 1989, Section III-B), in
+ * the natural-log domain: delta_0(k) = log v0_k + log e_k(o_0),
+ * delta_t(j) = max_i [delta_{t-1}(i) + log P_ij] + log e_j(o_t), with the
+ * smallest maximising i kept as the back-pointer, the path ending in the
+ * smallest maximising state. Writes path[T]; returns the path's log joint
+ * probability log p(s, o) (-inf when every path has probability zero).
+ */
+double oracle_viterbi(int K, const float *pi, const float *P, const float *p, const float *mu,
+                      const float *cov, int64_t T, const float *xy, const uint8_t *tremor, int init_mode,
+                      int32_t *path)
+{
+    if (T == 0) return 0.0;
+    double *d = (double *)malloc(sizeof(double) * K);
+    double *nd = (double *)malloc(sizeof(double) * K);
+    double *le = (double *)malloc(sizeof(double) * K);
+    int32_t *bp = (int32_t *)malloc(sizeof(int32_t) * (size_t)T * K);
+    initial_vector(K, pi, P, init_mode, d);
+    log_emissions(K, p, mu, cov, tremor[0], xy[0], xy[1], le);
+    for (int k = 0; k < K; ++k) d[k] = log(d[k]) + le[k];
+    for (int64_t t = 1; t < T; ++t) {
+        log_emissions(K, p, mu, cov, tremor[t], xy[2 * t], xy[2 * t + 1], le);
+        for (int j = 0; j < K; ++j) {
+            double best = -INFINITY;
+            int arg = 0;
+            for (int i = 0; i < K; ++i) {
+                double v = d[i] + log((double)P[i * K + j]);
+                if (v > best) { best = v; arg = i; }
+            }
+            nd[j] = best + le[j];
+            bp[t * K + j] = arg;
+        }
+        memcpy(d, nd, sizeof(double) * K);
+    }
+    double best = -INFINITY;
+    int arg = 0;
+    for (int k = 0; k < K; ++k)
+        if (d[k] > best) { best = d[k]; arg = k; }
+    path[T - 1] = arg;
+    for (int64_t t = T - 1; t >= 1; --t) path[t - 1] = bp[t * K + path[t]];
+    free(d); free(nd); free(le); free(bp);
+    return best;
+}
+
+/* log p(s, o) of a given hidden path (the joint probability of path and data) */
+double oracle_path_logjoint(int K, const float *pi, const float *P, const float *p, const float *mu,
+                            const float *cov, int64_t T, const float *xy, const uint8_t *tremor, int init_mode,
+                            const int32_t *path)
+{
+    if (T == 0) return 0.0;
+    double *v0 = (double *)malloc(sizeof(double) * K);
+    double *le = (double *)malloc(sizeof(double) * K);
+    initial_vector(K, pi, P, init_mode, v0);
+    log_emissions(K, p, mu, cov, tremor[0], xy[0], xy[1], le);
+    double s = log(v0[path[0]]) + le[path[0]];
+    for (int64_t t = 1; t < T; ++t) {
+        log_emissions(K, p, mu, cov, tremor[t], xy[2 * t], xy[2 * t + 1], le);
+        s += log((double)P[path[t - 1] * K + path[t]]) + le[path[t]];
+    }
+    free(v0); free(le);
+    return s;
+}
