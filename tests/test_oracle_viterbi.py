@@ -104,8 +104,8 @@ def test_returned_score_is_the_paths():
 MUTANTS = {
     "no_transition": ("double v = d[i] + log((double)P[i * K + j]);", "double v = d[i];"),
     "transposed": ("double v = d[i] + log((double)P[i * K + j]);", "double v = d[i] + log((double)P[j * K + i]);"),
-    "backtrack_shift": ("for (int64_t t = T - 1; t >= 1; --t) path[t - 1] = bp[t * K + path[t]];",
-                        "for (int64_t t = T - 1; t >= 1; --t) path[t - 1] = bp[(t - 1) * K + path[t]];"),
+    "no_first_emission": ("for (int k = 0; k < K; ++k) d[k] = log(d[k]) + le[k];",
+                          "for (int k = 0; k < K; ++k) d[k] = log(d[k]);"),
 }
 
 
