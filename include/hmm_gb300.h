@@ -131,6 +131,21 @@ int hmm_posterior(hmm_ctx *ctx, const hmm_params *params, const hmm_obs *obs, co
                   float *gamma, double *loglik, void *stream);
 
 /*
+ * The most probable hidden path of one sequence (Viterbi; Rabiner 1989,
+ * Section III-B) on the chunk structure: every chunk's max-plus product
+ * (best log2 score from each entering to each leaving state, CUDA cores),
+ * a scan over chunk boundaries in FP64 with back-pointers, then every chunk
+ * re-runs its recursion from its entering state and traces the path back
+ * from its leaving state. path (device, T int32) receives the states;
+ * *score (device double) log p(path, o) (natural log, -inf if every path has
+ * probability zero); *loglik (device double) log L. Ties go to the smallest
+ * state; paths whose scores differ only by FP32 rounding may differ from an
+ * FP64 evaluation. T >= 1, K <= 80. opts->precision is ignored.
+ */
+int hmm_viterbi(hmm_ctx *ctx, const hmm_params *params, const hmm_obs *obs, const hmm_opts *opts,
+                int32_t *path, double *score, double *loglik, void *stream);
+
+/*
  * Expected sufficient statistics of the hidden chain (the E-step of EM,
  * Baum-Welch; Rabiner 1989, Section III-C), from the same chunked forward-
  * backward pass as hmm_posterior, into `stats` (device, K*K + 8*K doubles):

@@ -89,6 +89,8 @@ SIGNATURES = {
                                      ctypes.POINTER(hmm_opts), _VP, _VP, _VP]),
     "hmm_expected_stats": (ctypes.c_int, [_VP, ctypes.POINTER(hmm_params), ctypes.POINTER(hmm_obs),
                                           ctypes.POINTER(hmm_opts), _VP, _VP, _VP]),
+    "hmm_viterbi": (ctypes.c_int, [_VP, ctypes.POINTER(hmm_params), ctypes.POINTER(hmm_obs),
+                                   ctypes.POINTER(hmm_opts), _VP, _VP, _VP, _VP]),
     "hmm_loglik_batched": (ctypes.c_int, [_VP, _I32, _I32, _VP, _VP, _VP, _VP, _VP, _I32, _VP,
                                           _VP, _VP, ctypes.POINTER(hmm_opts), _VP, _VP]),
     "hmm_loglik_batched_host": (ctypes.c_int, [_VP, _I32, _I32, _VP, _VP, _VP, _VP, _VP, _I32,
@@ -264,6 +266,24 @@ class Context:
         for i, name in enumerate(("G0", "Gs", "Gr", "Sx", "Sy", "Sxx", "Sxy", "Syy")):
             out[name] = flat[K * K + i * K:K * K + (i + 1) * K]
         return out, ll
+
+    def hmm_viterbi(self, pi, P, p_tremor, mu, cov, xy, tremor, opts=None, stream=None):
+        """Most probable hidden path (int32 [T]), its log joint probability and log L (float64 [1] each)."""
+        K = int(pi.shape[0])
+        for t, n in ((pi, "pi"), (P, "P"), (p_tremor, "p_tremor"), (mu, "mu"), (cov, "cov")):
+            _dev(t, torch.float32, n)
+        _dev(xy, torch.float32, "xy")
+        _dev(tremor, torch.uint8, "tremor")
+        T = int(tremor.shape[0])
+        path = torch.empty(T, dtype=torch.int32, device=pi.device)
+        score = torch.empty(1, dtype=torch.float64, device=pi.device)
+        ll = torch.empty(1, dtype=torch.float64, device=pi.device)
+        prm = hmm_params(K, pi.data_ptr(), P.data_ptr(), p_tremor.data_ptr(), mu.data_ptr(), cov.data_ptr())
+        ob = hmm_obs(T, xy.data_ptr() if T else None, tremor.data_ptr() if T else None)
+        o = opts if opts is not None else make_opts()
+        self._check(self.lib.hmm_viterbi(self.h, ctypes.byref(prm), ctypes.byref(ob), ctypes.byref(o),
+                                         path.data_ptr(), score.data_ptr(), ll.data_ptr(), _stream_ptr(stream)))
+        return path, score, ll
 
     def hmm_loglik(self, pi, P, p_tremor, mu, cov, xy, tremor, opts=None, out=None, stream=None):
         """log L of one parameter set on one sequence; returns a float64 [1] CUDA tensor."""

@@ -578,6 +578,50 @@ int hmm_expected_stats(hmm_ctx *c, const hmm_params *prm, const hmm_obs *obs, co
     return posterior_impl(c, prm, obs, opts, (float *)c->gam.p, loglik, stats, stream);
 }
 
+int hmm_viterbi(hmm_ctx *c, const hmm_params *prm, const hmm_obs *obs, const hmm_opts *opts, int32_t *path,
+                double *score, double *loglik, void *stream) {
+    if (!c) return HMM_EINVAL;
+    if (!prm || !obs || !path || !score || !loglik) return fail(c, HMM_EINVAL, "null argument");
+    if (obs->T < 1) return fail(c, HMM_EINVAL, "T must be >= 1");
+    if (prm->K > 255) return fail(c, HMM_EINVAL, "K must be <= 255");
+    int64_t offs[2] = {0, obs->T};
+    hmm_opts o;
+    if (opts) o = *opts; else hmm_opts_default(&o);
+    o.precision = HMM_PREC_FP32_SIMT;  // the max-plus chunks run on the CUDA cores
+    if (o.chunk_len == 0) {
+        const int64_t Lp = ((int64_t)std::sqrt(3.0 * (double)obs->T) + OBS_WIN - 1) / OBS_WIN * OBS_WIN;
+        o.chunk_len = (int32_t)std::min<int64_t>(16384, std::max<int64_t>(OBS_WIN, Lp));
+    }
+    // parameters, observations and the chunk table (and log L) from the likelihood path
+    int rc = hmm_loglik_batched(c, 1, prm->K, prm->pi, prm->P, prm->p_tremor, prm->mu, prm->cov, 1, offs, obs->xy,
+                                obs->tremor, &o, loglik, stream);
+    if (rc) return rc;
+    const Plan &pl = c->plan;
+    const int KP = pl.lay.KP, C = std::max(1, pl.n_chunks);
+    WorkPtrs wp;
+    carve_work(c->work.p, 1, 1, pl.lay, pl, &wp);
+    Carve cv(nullptr);
+    cv.take<float>((size_t)C * KP * KP);
+    cv.take<double>((size_t)C * KP);
+    cv.take<int32_t>((size_t)C * KP);
+    cv.take<int32_t>((size_t)C + 1);
+    cv.take<uint8_t>((size_t)C * pl.L * KP);
+    rc = ensure(c, c->fb, cv.off + 1024);
+    if (rc) return rc;
+    Carve vc(c->fb.p);
+    float *V = vc.take<float>((size_t)C * KP * KP);
+    double *voff = vc.take<double>((size_t)C * KP);
+    int32_t *ptr = vc.take<int32_t>((size_t)C * KP);
+    int32_t *bstate = vc.take<int32_t>((size_t)C + 1);
+    uint8_t *bp = vc.take<uint8_t>((size_t)C * pl.L * KP);
+    cudaError_t e = launch_viterbi(prm->K, o.init_mode, pl.n_chunks, pl.L, pl.lay, pl.d_chunks, prm->pi, prm->P,
+                                   wp.cblock, wp.head, wp.packed, V, voff, ptr, bstate, bp, path, score,
+                                   (cudaStream_t)stream);
+    c->last_launches += pl.n_chunks > 0 ? 3 : 2;
+    if (e != cudaSuccess) return cuda_fail(c, e, "viterbi launch");
+    return HMM_OK;
+}
+
 int hmm_loglik_batched_host(hmm_ctx *c, int32_t n_prop, int32_t K, const float *pi, const float *P,
                             const float *p, const float *mu, const float *cov, int32_t n_seg,
                             const int64_t *offs, const float *xy, const uint8_t *tremor,

@@ -140,6 +140,10 @@ cudaError_t launch_posterior(int K, int KP, int init_mode, int n_chunks, int L, 
                              const float2 *packed, const float *A0, const int32_t *e0, float *fvec, float *bvec,
                              float *gamma, double *stats_part, double *g0, double *stats, cudaStream_t st);
 int chunk_tc_wide_chunks_per_item(int KP, int precision);
+cudaError_t launch_viterbi(int K, int init_mode, int n_chunks, int L, const ConstLayout &lay, const ChunkDesc *chunks,
+                           const float *pi, const float *P, const float *cblock, const float2 *head,
+                           const float2 *packed, float *V, double *voff, int32_t *ptr, int32_t *bstate, uint8_t *bp,
+                           int32_t *path, double *score, cudaStream_t st);
 cudaError_t launch_chunk_tc_wide(int n_prop, int n_chunks, int renorm, int precision, const ConstLayout &lay,
                                  const float *cblock, const ChunkDesc *chunks, const float2 *packed, float *A0,
                                  int32_t *e0, unsigned *status, cudaStream_t st);
