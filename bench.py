@@ -15,6 +15,11 @@ Also reported on the same line:
                 the timed region);
   roofline      the chunk-product kernel against its peak;
   cpu_baseline  the FP64 CPU oracle on a bounded sample, on the host cores;
+  runlen        the run-length shortcut (FP32, not in the paper) on a
+                sparse-tremor workload of the same size (tremor probabilities
+                0.002-0.05, long no-tremor runs) beside the tensor-core path on
+                the same data; its arithmetic depends on the data, so it is
+                reported apart from the roofline;
   mcmc          effective samples per second of the log posterior and of
                 label-invariant summaries: the random-walk sampler, the learned
                 (MLP) proposal trained on the random walk's own history, and
@@ -61,6 +66,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-mcmc", action="store_true")
+    ap.add_argument("--no-runlen", action="store_true")
+    ap.add_argument("--runlen-min", type=int, default=4)
     ap.add_argument("--no-peaks", action="store_true")
     ap.add_argument("--mcmc-K", type=int, default=16)
     ap.add_argument("--mcmc-T", type=int, default=16384)
@@ -232,6 +239,70 @@ def run_reference(args):
     }))
 
 
+def _quiet_runs(tremor, offsets):
+    """Lengths of the maximal no-tremor runs among the chain steps (a
+    segment's first observation is not a chain step)."""
+    out = []
+    for s in range(len(offsets) - 1):
+        fl = np.asarray(tremor[offsets[s] + 1:offsets[s + 1]], np.int64)
+        z = np.concatenate([[1], fl, [1]])
+        out.append(np.diff(np.flatnonzero(z)) - 1)
+    r = np.concatenate(out) if out else np.zeros(0, np.int64)
+    return r[r > 0]
+
+
+def runlen_leg(args, api, synth, ctx, stream, flush, world, rank):
+    import torch
+    d = synth.batched_inputs(K=args.K, T=args.T, n_prop=args.n_prop, seed=rank_seed(args.seed + 100, rank),
+                             sparse=True)
+    dev = api.to_device(d["params"])
+    xy = torch.from_numpy(d["xy"]).cuda()
+    fl = torch.from_numpy(d["tremor"]).cuda()
+    offs = d["offsets"]
+    res = {"workload": f"sparse-tremor HMM log-likelihood, K={args.K}, T={args.T}, {args.n_prop} proposals, "
+                       f"tremor probabilities U{synth.SPARSE_P_RANGE}",
+           "runlen_min": args.runlen_min, "unit": UNIT}
+
+    def timed(opts, reps=3):
+        o = torch.empty(args.n_prop, dtype=torch.float64, device="cuda")
+        ctx.hmm_loglik_batched(*dev, offs, xy, fl, opts=opts, out=o)
+        torch.cuda.synchronize()
+        ms = 0.0
+        for i in range(reps):
+            flush.fill_(i & 0xff)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.hmm_loglik_batched(*dev, offs, xy, fl, opts=opts, out=o)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        ms = max_over_ranks(ms, world, "cuda") / reps
+        return ms, o
+
+    rms, rout = timed(api.make_opts(precision="fp32", runlen_min=args.runlen_min))
+    res["value"] = world * args.n_prop / (rms / 1e3)
+    res["ms_per_step"] = rms
+    res["launches_per_step"] = ctx.last_launch_count
+    tms, tout = timed(api.make_opts(precision=args.precision))
+    res["tc_same_data"] = {"precision": args.precision, "value": world * args.n_prop / (tms / 1e3),
+                           "ms_per_step": tms}
+    res["speedup_vs_tc"] = tms / rms
+    # the arithmetic the shortcut saves, counted on the host (runs are not
+    # cut at chunk boundaries here, so this slightly overstates the saving)
+    runs = _quiet_runs(d["tremor"], offs)
+    steps = int(offs[-1]) - (len(offs) - 1)
+    long = runs[runs >= args.runlen_min]
+    pops = sum(bin(int(n)).count("1") for n in long)
+    res["chain_steps"] = steps
+    res["steps_in_long_runs"] = int(long.sum())
+    res["matrix_products_per_eval_approx"] = int(steps - long.sum() + pops)
+    res["mean_quiet_run"] = float(runs.mean()) if runs.size else 0.0
+    res["max_abs_diff_vs_tc"] = float((rout - tout).abs().max().item())
+    res["max_rel_diff_vs_tc"] = float(((rout - tout).abs() / tout.abs()).max().item())
+    return res
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -355,6 +426,10 @@ def main():
         d = (out[:n_plain] - pout).abs().max().item()
         result["plain_gpu"]["max_abs_diff_vs_tc"] = d
         plain_out = pout.cpu().numpy()
+
+    # run-length shortcut on the sparse-tremor workload of the same size
+    if not args.no_runlen:
+        result["runlen"] = runlen_leg(args, api, synth, ctx, stream, flush, world, rank)
 
     # end to end through the host-buffer entry point
     if not args.no_e2e:

@@ -92,8 +92,24 @@ typedef struct {
     int32_t chunk_len;    /* steps per chunk product; 0 = chosen by the library   */
     int32_t renorm_every; /* per-row power-of-two renormalisation interval; 0 = 4 */
     int32_t recheck_fp32; /* batched: re-evaluate flagged proposals in FP32-SIMT   */
-    int32_t reserved[3];  /* must be 0                                             */
+    int32_t runlen_min;   /* run-length shortcut, FP32-SIMT only; 0 = off (below)  */
+    int32_t reserved[2];  /* must be 0                                             */
 } hmm_opts;
+
+/*
+ * Run-length shortcut (opts->runlen_min = n_min >= 1). Every step without a
+ * tremor has the same matrix M_0 = P diag(1 - p_k) (Eq. "emission-matrix"),
+ * so a run of n of them inside a chunk contributes M_0^n. With the shortcut
+ * on, the library first builds, per proposal, M_0^(2^b) for b = 0 ..
+ * floor(log2(chunk length)) by repeated squaring (each row a float row plus
+ * its own power-of-two exponent), and every run of at least n_min
+ * no-tremor steps is applied as the product of the powers of its length's
+ * set bits: popcount(n) matrix products instead of n. The result is the same
+ * likelihood up to rounding; the work, and therefore the speed, depends on
+ * the run lengths of the data. FP32-SIMT only (another precision with the
+ * shortcut returns HMM_EUNSUPPORTED); n_min in 1..16384, else HMM_EINVAL.
+ * Not part of the paper's algorithm.
+ */
 
 /* Default options: FP32-SIMT, emit-first, automatic chunking, renorm every 4. */
 void hmm_opts_default(hmm_opts *opts);

@@ -51,7 +51,8 @@ class HMMError(RuntimeError):
 class hmm_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("init_mode", ctypes.c_int32),
                 ("chunk_len", ctypes.c_int32), ("renorm_every", ctypes.c_int32),
-                ("recheck_fp32", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("recheck_fp32", ctypes.c_int32), ("runlen_min", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class hmm_params(ctypes.Structure):
@@ -151,7 +152,10 @@ def load_library(path=None) -> ctypes.CDLL:
 
 
 def make_opts(precision="fp32", init_mode=HMM_INIT_EMIT_FIRST, chunk_len=0, renorm_every=0,
-              recheck_fp32=0) -> hmm_opts:
+              recheck_fp32=0, runlen_min=0) -> hmm_opts:
+    """Options for every entry point; runlen_min > 0 turns on the run-length
+    shortcut (FP32 only): runs of at least that many no-tremor steps are
+    applied as products of precomputed binary powers of P diag(1 - p)."""
     o = hmm_opts()
     load_library().hmm_opts_default(ctypes.byref(o))
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -159,6 +163,7 @@ def make_opts(precision="fp32", init_mode=HMM_INIT_EMIT_FIRST, chunk_len=0, reno
     o.chunk_len = int(chunk_len)
     o.renorm_every = int(renorm_every)
     o.recheck_fp32 = int(recheck_fp32)
+    o.runlen_min = int(runlen_min)
     return o
 
 

@@ -432,14 +432,18 @@ int hmm_loglik_batched(hmm_ctx *c, int32_t n_prop, int32_t K, const float *pi, c
         return fail(c, HMM_EINVAL, "chunk_len must be 0 or a positive multiple of %d", OBS_WIN);
     if (opts.renorm_every < 0 || opts.renorm_every > 64)
         return fail(c, HMM_EINVAL, "renorm_every must be 0..64");
-    for (int r = 0; r < 3; ++r)
+    for (int r = 0; r < 2; ++r)
         if (opts.reserved[r]) return fail(c, HMM_EINVAL, "reserved option fields must be 0");
+    const int min_run = opts.runlen_min;
+    if (min_run < 0 || min_run > 16384) return fail(c, HMM_EINVAL, "runlen_min must be 0..16384");
     const int prec = opts.precision;
     if (prec != HMM_PREC_FP32_SIMT && prec != HMM_PREC_TF32 && prec != HMM_PREC_BF16 &&
         prec != HMM_PREC_TF32_SPLIT)
         return fail(c, HMM_EINVAL, "bad precision %d", prec);
     if (prec != HMM_PREC_FP32_SIMT && !chunk_tc_supported(K, prec))
         return fail(c, HMM_EUNSUPPORTED, "tensor-core path does not support K=%d precision %d", K, prec);
+    if (min_run && prec != HMM_PREC_FP32_SIMT)
+        return fail(c, HMM_EUNSUPPORTED, "the run-length shortcut runs on the FP32-SIMT path only");
     const int renorm = opts.renorm_every ? opts.renorm_every : 4;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaSetDevice(c->device);
@@ -466,9 +470,16 @@ int hmm_loglik_batched(hmm_ctx *c, int32_t n_prop, int32_t K, const float *pi, c
     // ---- workspace ----
     const int KP = lay.KP;
     WorkPtrs wp;
-    int rc = ensure(c, c->work, carve_work(nullptr, n_prop, n_seg, lay, pl, &wp) + 4096);
+    const size_t main_bytes = (carve_work(nullptr, n_prop, n_seg, lay, pl, &wp) + 255) & ~(size_t)255;
+    // run-length table after the main carve (the other entry points never see it)
+    const int nb = min_run ? rle_levels(L) : 0;
+    const size_t qtab_bytes = ((size_t)n_prop * nb * KP * KP * sizeof(float) + 255) & ~(size_t)255;
+    const size_t qexp_bytes = (size_t)n_prop * nb * KP * sizeof(int32_t);
+    int rc = ensure(c, c->work, main_bytes + qtab_bytes + qexp_bytes + 4096);
     if (rc) return rc;
     carve_work(c->work.p, n_prop, n_seg, lay, pl, &wp);
+    float *qtab = (float *)((char *)c->work.p + main_bytes);
+    int32_t *qexp = (int32_t *)((char *)c->work.p + main_bytes + qtab_bytes);
     float *cblock = wp.cblock;
     int *prop_bad = wp.prop_bad;
     int *obs_bad = wp.obs_bad;
@@ -486,7 +497,13 @@ int hmm_loglik_batched(hmm_ctx *c, int32_t n_prop, int32_t K, const float *pi, c
     if (e == cudaSuccess && T_total > 0) { e = launch_pack(n_seg, pl.d_offsets, pl.d_pbase, T_total, xy, tremor, packed, head, obs_bad, c->d_status, st); ++launches; }
     prof_mark(c, HMM_PHASE_CHUNK, st);
     if (e == cudaSuccess && pl.n_chunks > 0) {
-        if (prec == HMM_PREC_FP32_SIMT)
+        if (min_run) {
+            e = launch_rle_table(n_prop, nb, lay, cblock, qtab, qexp, c->d_status, st);
+            ++launches;
+            if (e == cudaSuccess)
+                e = launch_chunk_rle(n_prop, pl.n_chunks, renorm, min_run, nb, lay, cblock, qtab, qexp, pl.d_chunks,
+                                     packed, lv.A[0], (int32_t *)lv.e[0], c->d_status, st);
+        } else if (prec == HMM_PREC_FP32_SIMT)
             e = launch_chunk_simt(n_prop, pl.n_chunks, L, renorm, lay, cblock, pl.d_chunks, packed, lv.A[0], (int32_t *)lv.e[0], c->d_status, st);
         else
             e = launch_chunk_tc(n_prop, pl.n_chunks, L, renorm, prec, lay, cblock, pl.d_chunks, packed, lv.A[0], (int32_t *)lv.e[0], c->d_status, st);

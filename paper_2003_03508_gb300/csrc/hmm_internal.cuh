@@ -13,6 +13,8 @@
 //   A0/e0   [n_prop][n_chunks]     chunk products (KP x KP f32) and per-row
 //                                  int32 power-of-two exponents.
 //   A_l/e_l levels of the product tree (int64 exponents).
+//   qtab/qexp [n_prop][nb] run-length shortcut table (KP x KP f32 and KP int32
+//                                  row exponents per power), only when it is on.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -98,11 +100,6 @@ __device__ __forceinline__ float pow2f(int k) {
     return __int_as_float((k + 127) << 23);
 }
 
-// 2^d for an int64 d <= 0 (flushes below the normal range to zero)
-__device__ __forceinline__ float pow2f_nonpos(long long d) {
-    return d >= -126 ? __int_as_float((int)(d + 127) << 23) : 0.0f;
-}
-
 // log2 of the emission of state k for observation (x, y) (Eq. "emission-matrix").
 __device__ __forceinline__ float log2_emission(const float *__restrict__ em, int KP, int k,
                                                float x, float y, bool tremor) {
@@ -132,6 +129,15 @@ cudaError_t launch_pack(int n_seg, const int64_t *d_offsets, const int64_t *d_pb
 cudaError_t launch_chunk_simt(int n_prop, int n_chunks, int L, int renorm, const ConstLayout &lay,
                               const float *cblock, const ChunkDesc *chunks, const float2 *packed,
                               float *A0, int32_t *e0, unsigned *status, cudaStream_t st);
+
+// run-length shortcut (FP32 on the CUDA cores): table of M_0^(2^b), b < nb,
+// then chunk products that apply runs of >= min_run no-tremor steps from it
+int rle_levels(int L);
+cudaError_t launch_rle_table(int n_prop, int nb, const ConstLayout &lay, const float *cblock, float *qtab,
+                             int32_t *qexp, unsigned *status, cudaStream_t st);
+cudaError_t launch_chunk_rle(int n_prop, int n_chunks, int renorm, int min_run, int nb, const ConstLayout &lay,
+                             const float *cblock, const float *qtab, const int32_t *qexp, const ChunkDesc *chunks,
+                             const float2 *packed, float *A0, int32_t *e0, unsigned *status, cudaStream_t st);
 
 bool chunk_tc_supported(int K, int precision);
 int chunk_tc_chunks_per_item(int KP, int precision);

@@ -5,11 +5,15 @@
 // tree_level: one CTA multiplies up to TREE_GROUP consecutive products of one
 //   (proposal, segment) in order, X <- X * Y, keeping a power-of-two exponent
 //   per row: with X = diag(2^ex) X~ and Y = diag(2^ey) Y~,
-//     X Y = diag(2^(ex + m)) X~ diag(2^(ey - m)) Y~,   m = max_k ey_k,
-//   so Y~'s rows are scaled by 2^(ey_k - m) <= 1 before the product, and
-//   every row of the result is renormalised to [1, 2) afterwards. Exponents
-//   are int64 (exact). The grouping is fixed by the chunk count, so the
-//   result does not depend on scheduling.
+//     row i of X Y = 2^(ex_i + m_i) sum_k (X~_ik 2^(ey_k - m_i)) Y~_k,
+//     m_i = max over the k with X~_ik > 0 of (ey_k + exponent of X~_ik),
+//   so every term of row i is at most 2 and the largest is at least 1; a term
+//   that falls below the float range next to it is negligible in that row's
+//   sum. The alignment is per row of the result: rows of Y can differ in
+//   scale by far more than the float range (a reducible P), and a row of the
+//   result may draw only on the small ones. Every row of the result is then
+//   renormalised to [1, 2). Exponents are int64 (exact). The grouping is
+//   fixed by the chunk count, so the result does not depend on scheduling.
 // final: per proposal, per segment in order, the head vector
 //   h_k = pi0_k e_k(x_0) (pi0 = pi, or P^T pi for the transition-first form)
 //   is formed in FP64 and combined with the segment's product:
@@ -33,7 +37,7 @@ tree_level_kernel(int KP, int level, const TreeGroup *__restrict__ groups, Level
     float *Y = X + KP * KP;
     long long *ex = reinterpret_cast<long long *>(Y + KP * KP);
     long long *ey = ex + KP;
-    __shared__ long long sM;
+    long long *mrow = ey + KP;  // m_i of the current product
 
     const int q = blockIdx.y;
     const TreeGroup g = groups[blockIdx.x];
@@ -59,21 +63,33 @@ tree_level_kernel(int KP, int level, const TreeGroup *__restrict__ groups, Level
     for (int m = 1; m < g.cnt; ++m) {
         const size_t src = (size_t)g.src + m;
         for (int k = tid; k < KP; k += TREE_THREADS) ey[k] = load_e(src, k);
+        for (int idx = tid; idx < KP * KP; idx += TREE_THREADS) Y[idx] = Ain[src * KP * KP + idx];
         __syncthreads();
-        if (warp == 0) {
+        // per row of X (warp per row): m_i, then X~_ik <- X~_ik 2^(ey_k - m_i)
+        for (int i = warp; i < KP; i += nwarps) {
             long long mm = LLONG_MIN;
-            for (int k = lane; k < KP; k += 32) mm = ey[k] > mm ? ey[k] : mm;
+            for (int k = lane; k < KP; k += 32) {
+                const float x = X[i * KP + k];
+                if (x > 0.0f && ey[k] != ZERO_ROW_EXP64) {
+                    const long long v = ey[k] + float_exponent(x);
+                    mm = v > mm ? v : mm;
+                }
+            }
             for (int o = 16; o > 0; o >>= 1) {
                 long long other = __shfl_xor_sync(0xffffffffu, mm, o);
                 mm = other > mm ? other : mm;
             }
-            if (lane == 0) sM = mm;
-        }
-        __syncthreads();
-        const long long M = sM;
-        for (int idx = tid; idx < KP * KP; idx += TREE_THREADS) {
-            int k = idx / KP;
-            Y[idx] = Ain[src * KP * KP + idx] * pow2f_nonpos(ey[k] - M);
+            for (int k = lane; k < KP; k += 32) {
+                const float x = X[i * KP + k];
+                float w = 0.0f;
+                if (mm != LLONG_MIN && x > 0.0f && ey[k] != ZERO_ROW_EXP64) {
+                    long long dd = ey[k] - mm;  // <= 127: x 2^dd <= 2
+                    dd = dd < -400 ? -400 : dd;
+                    w = ldexpf(x, (int)dd);
+                }
+                X[i * KP + k] = w;
+            }
+            if (lane == 0) mrow[i] = mm;
         }
         __syncthreads();
         // Z = X * Y, each thread a strided set of entries, held in registers
@@ -100,7 +116,7 @@ tree_level_kernel(int KP, int level, const TreeGroup *__restrict__ groups, Level
                 r = r < -126 ? -126 : (r > 126 ? 126 : r);
                 float s = pow2f(-r);
                 for (int j = lane; j < KP; j += 32) X[i * KP + j] *= s;
-                if (lane == 0) ex[i] += M + r;
+                if (lane == 0) ex[i] += mrow[i] + r;
             } else if (lane == 0) {
                 ex[i] = ZERO_ROW_EXP64;
             }
@@ -115,7 +131,7 @@ tree_level_kernel(int KP, int level, const TreeGroup *__restrict__ groups, Level
 cudaError_t launch_tree_level(int n_prop, int KP, int level, int n_groups, const TreeGroup *groups,
                               const LevelPtrs &lv, unsigned *status, cudaStream_t st) {
     if (n_groups == 0) return cudaSuccess;
-    size_t smem = (size_t)2 * KP * KP * sizeof(float) + 2 * KP * sizeof(long long);
+    size_t smem = (size_t)2 * KP * KP * sizeof(float) + 3 * KP * sizeof(long long);
     dim3 grid(n_groups, n_prop);
     if (level == 0) {
         cudaFuncSetAttribute(tree_level_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -248,15 +248,24 @@ def config_inputs(name: str, seed: int | None = None):
     raise KeyError(name)
 
 
+SPARSE_P_RANGE = (0.002, 0.05)
+
+
 def batched_inputs(K: int, T: int, n_prop: int, seed: int, n_seg: int = 1,
-                   quiescent: bool = False, scale: float = 0.02):
+                   quiescent: bool = False, scale: float = 0.02, sparse: bool = False):
     """n_prop perturbed proposals around one generating parameter set.
 
     With n_seg > 1 the observations are n_seg independent segments of uneven
-    (log-uniform) length summing to about T, shared by every proposal.
+    (log-uniform) length summing to about T, shared by every proposal. With
+    sparse=True every state's tremor probability is drawn from SPARSE_P_RANGE
+    instead (hours with a tremor are rare; no-tremor runs average 20 to 500
+    steps), the workload of the run-length shortcut.
     """
     rng = np.random.default_rng(seed)
-    gen = quiescent_params(K, rng) if quiescent else random_params(K, rng)
+    if sparse:
+        gen = random_params(K, rng, p_range=SPARSE_P_RANGE)
+    else:
+        gen = quiescent_params(K, rng) if quiescent else random_params(K, rng)
     if n_seg == 1:
         o = sample_observations(gen, T, rng)
         xy, fl, offs = o.xy, o.tremor, np.array([0, T], np.int64)

@@ -57,6 +57,20 @@ def test_opts_default_is_host_only(lib):
     o = api.hmm_opts()
     L.hmm_opts_default(ctypes.byref(o))
     assert o.precision == api.HMM_PREC_FP32_SIMT and o.init_mode == 0 and o.chunk_len == 0
+    assert o.runlen_min == 0 and list(o.reserved) == [0, 0]
+
+
+def test_opts_struct_matches_the_header():
+    # the binding's hmm_opts has the header's fields, in order, as int32
+    import re
+    from paper_2003_03508_gb300 import api
+    text = (ROOT / "include" / "hmm_gb300.h").read_text()
+    body = re.search(r"typedef struct \{([^}]*)\} hmm_opts;", text).group(1)
+    fields = re.findall(r"int32_t\s+(\w+)(?:\[(\d+)\])?;", body)
+    want = [(n, int(c) if c else 1) for n, c in fields]
+    got = [(n, getattr(t, "_length_", 1)) for n, t in api.hmm_opts._fields_]
+    assert got == want
+    assert ctypes.sizeof(api.hmm_opts) == 4 * sum(c for _, c in want)
 
 
 def test_host_argument_checks_without_gpu(lib):

@@ -198,3 +198,42 @@ def test_host_entry_point_matches_device(cuda_lib):
                                  torch.from_numpy(d["xy"]).cuda(), torch.from_numpy(d["tremor"]).cuda())
     host = ctx.hmm_loglik_batched_host(*d["params"].as_tuple(), d["offsets"], d["xy"], d["tremor"])
     assert np.array_equal(dev.cpu().numpy(), host)
+
+
+def _split_favourites():
+    """P = I, identical tremor locations for every state, p = (0.9, 0.001, 0.5,
+    0.02), and T = 2049: tremors at steps 0..1024, none after. The first half
+    favours the p = 0.9 state, the second the p = 0.001 state, and the whole
+    the p = 0.5 state -- by 2^868 and 2^1022 behind the favourite of each
+    half, far outside the float range."""
+    rng = np.random.default_rng(2900)
+    K = 4
+    prm = synth.random_params(K, rng)
+    prm.P[:] = np.eye(K, dtype=np.float32)
+    prm.p_tremor[:] = np.array([0.9, 0.001, 0.5, 0.02], np.float32)
+    prm.mu[:] = (150.0, 75.0)
+    prm.cov[:] = (100.0, 0.0, 100.0)
+    T = 2049
+    fl = np.zeros(T, np.uint8)
+    fl[:1025] = 1
+    xy = np.where(fl[:, None] == 1, rng.normal((150.0, 75.0), 10.0, (T, 2)), 0.0).astype(np.float32)
+    return prm, xy, fl
+
+
+def test_reducible_transitions_tree(cuda_lib):
+    # the product tree aligns every row of a product on its own scale: with
+    # one alignment per matrix the p = 0.5 row of the second half's product
+    # (2^1022 below its largest row) would flush, and with it the row that
+    # carries the likelihood
+    prm, xy, fl = _split_favourites()
+    ref = oracle.loglik(prm, xy, fl)
+    # closed form: log sum_k pi_k p_k^1025 (1 - p_k)^1024 + sum over tremors of log N(o_t)
+    p = prm.p_tremor.astype(np.float64)
+    terms = np.log(prm.pi.astype(np.float64)) + 1025 * np.log(p) + 1024 * np.log1p(-p)
+    d = xy[:1025].astype(np.float64) - (150.0, 75.0)
+    lgauss = -np.log(2 * np.pi * 100.0) - 0.5 * (d ** 2).sum(axis=1) / 100.0
+    want = terms.max() + math.log(np.exp(terms - terms.max()).sum()) + lgauss.sum()
+    assert abs(ref - want) < 1e-9 * abs(want), (ref, want)
+    for L in (1024, 64):  # 2 and 32 chunks: one and two tree levels
+        got = _gpu_loglik(cuda_lib, prm, xy, fl, chunk_len=L)
+        assert _close(got, ref), (L, got, ref)
