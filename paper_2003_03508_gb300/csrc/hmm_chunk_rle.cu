@@ -15,13 +15,19 @@
 // than the float range, so one exponent per matrix would flush whole rows
 // to zero.
 //
-// Chunk kernel (one CTA per chunk and proposal, one thread per row of the
-// running product): walks the chunk's steps like the FP32 chunk kernel;
-// at a step without a tremor it measures the run of no-tremor steps ahead
-// (one warp-wide ballot per 32 steps) and, when the run has at least
-// `min_run` steps, multiplies the running product by the table entries of
-// the run length's set bits and jumps past the run. Shorter runs take the
+// Chunk kernels (one thread per row of a chunk's running product): walk the
+// chunk's steps like the FP32 chunk kernel; at a step without a tremor they
+// measure the run of no-tremor steps ahead and, when it has at least
+// `min_run` steps, multiply the running product by the table entries of the
+// run length's set bits and jump past the run. Shorter runs take the
 // ordinary step and are not measured again.
+//   KP <= 32: one warp per chunk, WPC chunks of one proposal per CTA sharing
+//     P and the whole table in shared memory; the state's emission constants
+//     live in its lane's registers, the step's best emission is a warp
+//     reduction, and the observations come in 32-step windows held one per
+//     lane, whose ballot mask gives run lengths without further loads.
+//   KP > 32: one CTA per chunk (several warps per row set), table read
+//     through L1/L2, one warp ballot per 32 steps of a run.
 #include "hmm_internal.cuh"
 
 namespace hmm {
@@ -54,8 +60,8 @@ __device__ __forceinline__ bool renorm_row(float (&row)[KP], int &expo, bool &ba
 }
 
 // row <- row * (2^R Q), Q a KP x KP row-major float matrix (shared or
-// global memory) whose row k carries the exponent R[k] (ZERO_ROW_EXP32: the
-// row is zero). The terms
+// global memory, 16-byte aligned, as is R) whose row k carries the exponent
+// R[k] (ZERO_ROW_EXP32: the row is zero). The terms
 // row[k] 2^R[k] are aligned to the largest one before the product, so a
 // term far below it (where it cannot change the float sum) flushes to zero
 // instead of every term overflowing or underflowing together.
@@ -64,9 +70,14 @@ __device__ __forceinline__ void mul_scaled(float (&row)[KP], int &expo, const fl
                                            const int32_t *__restrict__ R) {
     int top = INT32_MIN;
 #pragma unroll
-    for (int k = 0; k < KP; ++k) {
-        const int rk = R[k];
-        if (row[k] > 0.0f && rk != ZERO_ROW_EXP32) top = max(top, rk + float_exponent(row[k]));
+    for (int k4 = 0; k4 < KP / 4; ++k4) {
+        const int4 v = reinterpret_cast<const int4 *>(R)[k4];
+        const int rv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = 4 * k4 + u;
+            if (row[k] > 0.0f && rv[u] != ZERO_ROW_EXP32) top = max(top, rv[u] + float_exponent(row[k]));
+        }
     }
     if (top == INT32_MIN) {  // nothing reaches a non-zero row: the product row is zero
 #pragma unroll
@@ -78,8 +89,16 @@ __device__ __forceinline__ void mul_scaled(float (&row)[KP], int &expo, const fl
     for (int j = 0; j < KP; ++j) nw[j] = 0.0f;
 #pragma unroll
     for (int k = 0; k < KP; ++k) {
-        const int rk = R[k];
-        const float w = (row[k] > 0.0f && rk != ZERO_ROW_EXP32) ? ldexpf(row[k], rk - top) : 0.0f;
+        // w = row[k] 2^(R[k] - top) <= 2, as two exact power-of-two factors
+        // (each within the normal exponent range); below 2^-252 it is zero
+        float w = 0.0f;
+        const int rk = R[k];  // reloaded (a broadcast load) rather than held in registers
+        if (row[k] > 0.0f && rk != ZERO_ROW_EXP32) {
+            const int d = rk - top;
+            const int d1 = d < -126 ? -126 : d;
+            const int d2 = d - d1 < -126 ? -126 : d - d1;
+            w = row[k] * pow2f(d1) * pow2f(d2);
+        }
         const float4 *qk = reinterpret_cast<const float4 *>(Q + k * KP);
 #pragma unroll
         for (int j4 = 0; j4 < KP / 4; ++j4) {
@@ -115,7 +134,7 @@ __global__ void __launch_bounds__(rle_threads<KP>())
 rle_table_kernel(int nb, ConstLayout lay, const float *__restrict__ cblock, float *__restrict__ qtab,
                  int32_t *__restrict__ qexp, unsigned *__restrict__ status) {
     __shared__ __align__(16) float sQ[KP * KP];
-    __shared__ int32_t sR[KP];
+    __shared__ __align__(16) int32_t sR[KP];
     const int q = blockIdx.x;
     const int i = threadIdx.x;
     const float *cb = cblock + (size_t)q * lay.stride;
@@ -293,6 +312,162 @@ chunk_rle_kernel(int n_chunks, int renorm, int min_run, int nb, ConstLayout lay,
     if (bad) atomicOr(status, ST_ENUMERIC);
 }
 
+constexpr int RLE_WPC = 8;  // chunks (warps) per CTA of the warp kernel
+
+template <int KP>
+__global__ void __launch_bounds__(32 * RLE_WPC, 2)
+chunk_rle_warp_kernel(int n_chunks, int renorm, int min_run, int nb, ConstLayout lay,
+                      const float *__restrict__ cblock, const float *__restrict__ qtab,
+                      const int32_t *__restrict__ qexp, const ChunkDesc *__restrict__ chunks,
+                      const float2 *__restrict__ packed, float *__restrict__ A0, int32_t *__restrict__ e0,
+                      unsigned *__restrict__ status) {
+    static_assert(KP <= 32, "one lane per row");
+    extern __shared__ __align__(16) float smem[];
+    float *sP = smem;                                   // KP x KP
+    float *sQ = sP + KP * KP;                           // nb x KP x KP
+    int32_t *sR = reinterpret_cast<int32_t *>(sQ + (size_t)nb * KP * KP);  // nb x KP
+    float *sD = reinterpret_cast<float *>(sR + (size_t)nb * KP);           // RLE_WPC x KP
+
+    const int q = blockIdx.y;
+    const int warp = threadIdx.x >> 5;
+    const int i = threadIdx.x & 31;  // row of the running product = lane
+    const int ch = blockIdx.x * RLE_WPC + warp;
+    const float *cb = cblock + (size_t)q * lay.stride;
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(cb + lay.off_p32);
+        for (int idx = threadIdx.x; idx < KP * KP / 4; idx += blockDim.x)
+            reinterpret_cast<float4 *>(sP)[idx] = src[idx];
+        const float4 *qsrc = reinterpret_cast<const float4 *>(qtab + (size_t)q * nb * KP * KP);
+        for (int idx = threadIdx.x; idx < nb * KP * KP / 4; idx += blockDim.x)
+            reinterpret_cast<float4 *>(sQ)[idx] = qsrc[idx];
+        const int32_t *rsrc = qexp + (size_t)q * nb * KP;
+        for (int idx = threadIdx.x; idx < nb * KP; idx += blockDim.x) sR[idx] = rsrc[idx];
+    }
+    __syncthreads();  // the only CTA-wide barrier
+    if (ch >= n_chunks) return;
+
+    // this lane's state's emission constants (lanes past KP never win the max)
+    const float *em = cb + lay.off_emis;
+    const bool owner = i < KP;
+    const float mux = owner ? em[EM_MUX * KP + i] : 0.f, muy = owner ? em[EM_MUY * KP + i] : 0.f;
+    const float qa = owner ? em[EM_QA * KP + i] : 0.f, qb = owner ? em[EM_QB * KP + i] : 0.f;
+    const float qc = owner ? em[EM_QC * KP + i] : 0.f;
+    const float ctr = owner ? em[EM_CTR * KP + i] : -INFINITY, cno = owner ? em[EM_CNO * KP + i] : -INFINITY;
+    float *wD = sD + warp * KP;
+
+    const ChunkDesc d = chunks[ch];
+    const float2 *obs = packed + d.pstart;
+    const int len = d.len;
+
+    float row[KP];
+#pragma unroll
+    for (int j = 0; j < KP; ++j) row[j] = (j == i) ? 1.0f : 0.0f;
+    int expo = 0;
+    bool bad = false;
+    int since = 0;
+    int measured = 0;
+    int w0 = -32;        // first step of the window held in the lanes
+    float2 ob = make_float2(0.f, 0.f);
+    unsigned quiet = 0;  // bit u: step w0 + u has no tremor
+
+    for (int t = 0; t < len;) {  // warp-uniform control flow throughout
+        if (t >= w0 + 32) {
+            w0 = t;
+            const int u = w0 + i;
+            ob = u < len ? obs[u] : make_float2(0.f, 0.f);
+            quiet = __ballot_sync(0xffffffffu, u < len && isnan(ob.x));
+        }
+        const int sft = t - w0;
+        const float ox = __shfl_sync(0xffffffffu, ob.x, sft);
+        const float oy = __shfl_sync(0xffffffffu, ob.y, sft);
+        const bool tremor = !isnan(ox);
+        if (!tremor && min_run > 0 && t >= measured) {
+            const unsigned rest = ~quiet >> sft;  // bit 0 is this (quiet) step
+            int n = rest ? __ffs(rest) - 1 : 32 - sft;
+            if (!rest && w0 + 32 < len) n += quiet_run(obs + w0 + 32, len - (w0 + 32));
+            if (n >= min_run) {
+                for (int b = 0; b < nb; ++b) {
+                    if (!((n >> b) & 1)) continue;
+                    mul_scaled<KP>(row, expo, sQ + (size_t)b * KP * KP, sR + (size_t)b * KP);
+                    if (!renorm_row<KP>(row, expo, bad)) break;
+                }
+                since = 0;
+                t += n;
+                measured = t;
+                continue;
+            }
+            measured = t + n;
+        }
+        // an ordinary step
+        float l;
+        if (!tremor) {
+            l = cno;
+        } else {
+            const float dx = ox - mux, dy = oy - muy;
+            l = fmaf(qa * dx, dx, fmaf(qb * dx, dy, fmaf(qc * dy, dy, ctr)));
+        }
+        float m = l;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        int E = 0;
+        float di = 0.0f;
+        if (m >= -(float)EXP_LIMIT) {
+            E = (int)floorf(m);
+            di = exp2f(l - (float)E);
+        } else if (m != -INFINITY) {
+            bad = true;
+        }
+        if (owner) wD[i] = di;
+        float nw[KP];
+#pragma unroll
+        for (int j = 0; j < KP; ++j) nw[j] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            const float rk = row[k];
+            const float4 *pk = reinterpret_cast<const float4 *>(sP + k * KP);
+#pragma unroll
+            for (int j4 = 0; j4 < KP / 4; ++j4) {
+                const float4 pv = pk[j4];
+                nw[4 * j4 + 0] = fmaf(rk, pv.x, nw[4 * j4 + 0]);
+                nw[4 * j4 + 1] = fmaf(rk, pv.y, nw[4 * j4 + 1]);
+                nw[4 * j4 + 2] = fmaf(rk, pv.z, nw[4 * j4 + 2]);
+                nw[4 * j4 + 3] = fmaf(rk, pv.w, nw[4 * j4 + 3]);
+            }
+        }
+        __syncwarp();  // wD complete
+        const float4 *dv = reinterpret_cast<const float4 *>(wD);
+#pragma unroll
+        for (int j4 = 0; j4 < KP / 4; ++j4) {
+            const float4 dd = dv[j4];
+            row[4 * j4 + 0] = nw[4 * j4 + 0] * dd.x;
+            row[4 * j4 + 1] = nw[4 * j4 + 1] * dd.y;
+            row[4 * j4 + 2] = nw[4 * j4 + 2] * dd.z;
+            row[4 * j4 + 3] = nw[4 * j4 + 3] * dd.w;
+        }
+        __syncwarp();  // wD read by every lane before the next step writes it
+        expo += E;
+        if (++since == renorm) {
+            renorm_row<KP>(row, expo, bad);
+            since = 0;
+        }
+        ++t;
+    }
+    if (owner) {
+        if (since > 0) renorm_row<KP>(row, expo, bad);
+        float mx = 0.0f;
+#pragma unroll
+        for (int j = 0; j < KP; ++j) mx = fmaxf(mx, row[j]);
+        if (!(mx > 0.0f)) expo = ZERO_ROW_EXP32;
+        float *dst = A0 + ((size_t)q * n_chunks + ch) * KP * KP + (size_t)i * KP;
+#pragma unroll
+        for (int j4 = 0; j4 < KP / 4; ++j4)
+            reinterpret_cast<float4 *>(dst)[j4] =
+                make_float4(row[4 * j4], row[4 * j4 + 1], row[4 * j4 + 2], row[4 * j4 + 3]);
+        e0[((size_t)q * n_chunks + ch) * KP + i] = expo;
+        if (bad) atomicOr(status, ST_ENUMERIC);
+    }
+}
+
 }  // namespace
 
 int rle_levels(int L) {
@@ -321,6 +496,26 @@ cudaError_t launch_chunk_rle(int n_prop, int n_chunks, int renorm, int min_run, 
                              const float *cblock, const float *qtab, const int32_t *qexp, const ChunkDesc *chunks,
                              const float2 *packed, float *A0, int32_t *e0, unsigned *status, cudaStream_t st) {
     if (n_chunks == 0 || n_prop == 0) return cudaSuccess;
+    if (lay.KP <= 32) {
+        const dim3 wgrid((n_chunks + RLE_WPC - 1) / RLE_WPC, n_prop);
+        const size_t smem = sizeof(float) * ((size_t)lay.KP * lay.KP * (1 + nb) + (size_t)nb * lay.KP +
+                                             (size_t)RLE_WPC * lay.KP);
+        switch (lay.KP) {
+#define HMM_RLE_W(KPV)                                                                                    \
+    case KPV: {                                                                                           \
+        cudaError_t e = cudaFuncSetAttribute(chunk_rle_warp_kernel<KPV>,                                  \
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
+        if (e != cudaSuccess) return e;                                                                   \
+        chunk_rle_warp_kernel<KPV><<<wgrid, 32 * RLE_WPC, smem, st>>>(n_chunks, renorm, min_run, nb, lay,  \
+                                                                      cblock, qtab, qexp, chunks, packed,  \
+                                                                      A0, e0, status);                    \
+        return cudaGetLastError();                                                                        \
+    }
+            HMM_RLE_W(4) HMM_RLE_W(8) HMM_RLE_W(16) HMM_RLE_W(32)
+#undef HMM_RLE_W
+            default: return cudaErrorInvalidValue;
+        }
+    }
     const dim3 grid(n_chunks, n_prop);
     switch (lay.KP) {
 #define HMM_RLE_C(KPV)                                                                                \
