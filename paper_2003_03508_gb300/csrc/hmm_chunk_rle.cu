@@ -114,6 +114,37 @@ __device__ __forceinline__ void mul_scaled(float (&row)[KP], int &expo, const fl
     expo += top;
 }
 
+// The first half of mul_scaled on its own: row[k] <- row[k] 2^(R[k] - top)
+// in place; returns top, or INT32_MIN after zeroing a row that reaches no
+// non-zero row of Q. R is 16-byte aligned.
+template <int KP>
+__device__ __forceinline__ int prescale_row(float (&row)[KP], const int32_t *__restrict__ R) {
+    int top = INT32_MIN;
+#pragma unroll
+    for (int k4 = 0; k4 < KP / 4; ++k4) {
+        const int4 v = reinterpret_cast<const int4 *>(R)[k4];
+        const int rv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = 4 * k4 + u;
+            if (row[k] > 0.0f && rv[u] != ZERO_ROW_EXP32) top = max(top, rv[u] + float_exponent(row[k]));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+        float w = 0.0f;
+        const int rk = R[k];
+        if (top != INT32_MIN && row[k] > 0.0f && rk != ZERO_ROW_EXP32) {
+            const int d = rk - top;
+            const int d1 = d < -126 ? -126 : d;
+            const int d2 = d - d1 < -126 ? -126 : d - d1;
+            w = row[k] * pow2f(d1) * pow2f(d2);
+        }
+        row[k] = w;
+    }
+    return top;
+}
+
 // Number of consecutive no-tremor steps at obs[0 ..], at most cap (cap >= 1).
 // Every lane of the calling warp must take part; all lanes return the same
 // value. At most cap / 32 + 1 iterations.
@@ -370,61 +401,76 @@ chunk_rle_warp_kernel(int n_chunks, int renorm, int min_run, int nb, ConstLayout
     float2 ob = make_float2(0.f, 0.f);
     unsigned quiet = 0;  // bit u: step w0 + u has no tremor
 
-    for (int t = 0; t < len;) {  // warp-uniform control flow throughout
-        if (t >= w0 + 32) {
-            w0 = t;
-            const int u = w0 + i;
-            ob = u < len ? obs[u] : make_float2(0.f, 0.f);
-            quiet = __ballot_sync(0xffffffffu, u < len && isnan(ob.x));
-        }
-        const int sft = t - w0;
-        const float ox = __shfl_sync(0xffffffffu, ob.x, sft);
-        const float oy = __shfl_sync(0xffffffffu, ob.y, sft);
-        const bool tremor = !isnan(ox);
-        if (!tremor && min_run > 0 && t >= measured) {
-            const unsigned rest = ~quiet >> sft;  // bit 0 is this (quiet) step
-            int n = rest ? __ffs(rest) - 1 : 32 - sft;
-            if (!rest && w0 + 32 < len) n += quiet_run(obs + w0 + 32, len - (w0 + 32));
-            if (n >= min_run) {
-                for (int b = 0; b < nb; ++b) {
-                    if (!((n >> b) & 1)) continue;
-                    mul_scaled<KP>(row, expo, sQ + (size_t)b * KP * KP, sR + (size_t)b * KP);
-                    if (!renorm_row<KP>(row, expo, bad)) break;
-                }
-                since = 0;
-                t += n;
-                measured = t;
-                continue;
-            }
-            measured = t + n;
-        }
-        // an ordinary step
-        float l;
-        if (!tremor) {
-            l = cno;
+    // One token per iteration: an ordinary step, or one table power of the run
+    // in progress (`pending` holds the powers still to apply). Both share the
+    // one copy of the K^3 product below, which keeps the loop small enough
+    // for the instruction cache. Control flow is warp-uniform throughout.
+    int pending = 0;
+    for (int t = 0; t < len || pending;) {
+        int boff;      // offset of the right operand in shared memory
+        int add;       // exponent this token adds to the row
+        bool ordinary;
+        if (pending) {
+            const int b = __ffs(pending) - 1;
+            pending &= pending - 1;
+            boff = (1 + b) * KP * KP;
+            add = prescale_row<KP>(row, sR + b * KP);
+            if (add == INT32_MIN) add = 0;  // the row is zero (and stays zero)
+            ordinary = false;
         } else {
-            const float dx = ox - mux, dy = oy - muy;
-            l = fmaf(qa * dx, dx, fmaf(qb * dx, dy, fmaf(qc * dy, dy, ctr)));
-        }
-        float m = l;
+            if (t >= w0 + 32) {
+                w0 = t;
+                const int u = w0 + i;
+                ob = u < len ? obs[u] : make_float2(0.f, 0.f);
+                quiet = __ballot_sync(0xffffffffu, u < len && isnan(ob.x));
+            }
+            const int sft = t - w0;
+            const float ox = __shfl_sync(0xffffffffu, ob.x, sft);
+            const float oy = __shfl_sync(0xffffffffu, ob.y, sft);
+            const bool tremor = !isnan(ox);
+            if (!tremor && min_run > 0 && t >= measured) {
+                const unsigned rest = ~quiet >> sft;  // bit 0 is this (quiet) step
+                int n = rest ? __ffs(rest) - 1 : 32 - sft;
+                if (!rest && w0 + 32 < len) n += quiet_run(obs + w0 + 32, len - (w0 + 32));
+                if (n >= min_run) {
+                    pending = n;
+                    t += n;
+                    measured = t;
+                    continue;
+                }
+                measured = t + n;
+            }
+            float l;
+            if (!tremor) {
+                l = cno;
+            } else {
+                const float dx = ox - mux, dy = oy - muy;
+                l = fmaf(qa * dx, dx, fmaf(qb * dx, dy, fmaf(qc * dy, dy, ctr)));
+            }
+            float m = l;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        int E = 0;
-        float di = 0.0f;
-        if (m >= -(float)EXP_LIMIT) {
-            E = (int)floorf(m);
-            di = exp2f(l - (float)E);
-        } else if (m != -INFINITY) {
-            bad = true;
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            int E = 0;
+            float di = 0.0f;
+            if (m >= -(float)EXP_LIMIT) {
+                E = (int)floorf(m);
+                di = exp2f(l - (float)E);
+            } else if (m != -INFINITY) {
+                bad = true;
+            }
+            if (owner) wD[i] = di;
+            boff = 0;
+            add = E;
+            ordinary = true;
         }
-        if (owner) wD[i] = di;
         float nw[KP];
 #pragma unroll
         for (int j = 0; j < KP; ++j) nw[j] = 0.0f;
+        const float *B = smem + boff;
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
             const float rk = row[k];
-            const float4 *pk = reinterpret_cast<const float4 *>(sP + k * KP);
+            const float4 *pk = reinterpret_cast<const float4 *>(B + k * KP);
 #pragma unroll
             for (int j4 = 0; j4 < KP / 4; ++j4) {
                 const float4 pv = pk[j4];
@@ -434,23 +480,28 @@ chunk_rle_warp_kernel(int n_chunks, int renorm, int min_run, int nb, ConstLayout
                 nw[4 * j4 + 3] = fmaf(rk, pv.w, nw[4 * j4 + 3]);
             }
         }
-        __syncwarp();  // wD complete
-        const float4 *dv = reinterpret_cast<const float4 *>(wD);
+        if (ordinary) {
+            __syncwarp();  // wD complete
+            const float4 *dv = reinterpret_cast<const float4 *>(wD);
 #pragma unroll
-        for (int j4 = 0; j4 < KP / 4; ++j4) {
-            const float4 dd = dv[j4];
-            row[4 * j4 + 0] = nw[4 * j4 + 0] * dd.x;
-            row[4 * j4 + 1] = nw[4 * j4 + 1] * dd.y;
-            row[4 * j4 + 2] = nw[4 * j4 + 2] * dd.z;
-            row[4 * j4 + 3] = nw[4 * j4 + 3] * dd.w;
+            for (int j4 = 0; j4 < KP / 4; ++j4) {
+                const float4 dd = dv[j4];
+                row[4 * j4 + 0] = nw[4 * j4 + 0] * dd.x;
+                row[4 * j4 + 1] = nw[4 * j4 + 1] * dd.y;
+                row[4 * j4 + 2] = nw[4 * j4 + 2] * dd.z;
+                row[4 * j4 + 3] = nw[4 * j4 + 3] * dd.w;
+            }
+            __syncwarp();  // wD read by every lane before the next step writes it
+            ++t;
+        } else {
+#pragma unroll
+            for (int j = 0; j < KP; ++j) row[j] = nw[j];
         }
-        __syncwarp();  // wD read by every lane before the next step writes it
-        expo += E;
-        if (++since == renorm) {
+        expo += add;
+        if (!ordinary || ++since == renorm) {
             renorm_row<KP>(row, expo, bad);
             since = 0;
         }
-        ++t;
     }
     if (owner) {
         if (since > 0) renorm_row<KP>(row, expo, bad);
