@@ -230,3 +230,23 @@ def test_full_size_sampled(cuda_lib):
     ref = oracle.loglik_batched(sub, d["xy"], d["tremor"], d["offsets"], n_threads=6)
     for j, q in enumerate(pick):
         assert _close(float(got[q]), float(ref[j])), (q, got[q], ref[j])
+
+
+def test_sparse_workload_tf32_split(cuda_lib):
+    # Tensor cores on the sparse-tremor workload: |log L| per step is ~13x
+    # smaller than on the random workload, so TF32's rounding of P (a per-step
+    # bias in log of up to ~1e-4) leaves the 1e-4 relative bar (2.6e-4
+    # measured); with P as TF32 hi + lo the bar holds (5e-6 measured).
+    api = cuda_lib
+    d = synth.batched_inputs(K=32, T=1 << 20, n_prop=64, seed=43, sparse=True)
+    ctx = api.default_context()
+    xy = torch.from_numpy(d["xy"]).cuda()
+    fl = torch.from_numpy(d["tremor"]).cuda()
+    got = ctx.hmm_loglik_batched(*api.to_device(d["params"]), d["offsets"], xy, fl,
+                                 opts=api.make_opts(precision="tf32_split")).cpu().numpy()
+    pick = [0, 31, 63]
+    sub = synth.HMMParams(*(a[pick] for a in d["params"].as_tuple()))
+    ref = oracle.loglik_batched(sub, d["xy"], d["tremor"], d["offsets"], n_threads=3)
+    rel = np.abs(got[pick] - ref) / np.abs(ref)
+    print("tf32_split sparse rel err", rel)
+    assert np.all(rel <= 1e-4), rel
