@@ -212,6 +212,13 @@ def cpu_baseline(inputs, n_sample, cores):
     return n_sample / dt, dt, np.asarray(ref, dtype=np.float64)
 
 
+def workload_config(args, n_seg=1):
+    """The workload as both arms name it in `config`."""
+    return {"workload": f"tremor HMM log-likelihood, K={args.K}, T={args.T}, "
+                        f"{args.n_prop} proposals batched per GPU",
+            "K": args.K, "T": args.T, "n_prop": args.n_prop, "n_seg": n_seg}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -227,13 +234,13 @@ def run_reference(args):
         times.append(dt)
     ms = 1e3 * statistics.mean(times)
     value = cores / (ms / 1e3)
-    sample = f"{cores} proposals x T={args.T} (K={args.K}) per step, one proposal per core"
+    sample = (f"{cores} of the {args.n_prop} proposals per step, full T={args.T} (K={args.K}), "
+              f"one proposal per core")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"tremor HMM log-likelihood K={args.K} T={args.T} batched proposals",
-                   "K": args.K, "T": args.T},
+        "config": workload_config(args),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -394,9 +401,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": f"tremor HMM log-likelihood, K={args.K}, T={args.T}, "
-                               f"{args.n_prop} proposals batched per GPU",
-                   "K": args.K, "T": args.T, "n_prop": args.n_prop, "n_seg": len(offs) - 1,
+        "config": {**workload_config(args, len(offs) - 1),
                    "precision": args.precision, "chunk_len": L,
                    "l2": "flushed between timed steps (256 MiB write)"},
         "roofline": roof,
