@@ -327,6 +327,8 @@ int hmm_destroy(hmm_ctx *c) {
     if (c->work.p) cudaFree(c->work.p);
     if (c->planbuf.p) cudaFree(c->planbuf.p);
     if (c->stage.p) cudaFree(c->stage.p);
+    if (c->fb.p) cudaFree(c->fb.p);
+    if (c->gam.p) cudaFree(c->gam.p);
     if (c->d_status) cudaFree(c->d_status);
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
