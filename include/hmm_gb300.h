@@ -226,6 +226,92 @@ int hmm_last_launch_count(const hmm_ctx *ctx);
  */
 int hmm_last_chunk_len(const hmm_ctx *ctx);
 
+/* ---- chunk-length tuning of the batched schedule ----
+ *
+ * Section "The likelihood algorithm" splits the matrix chain into chunks
+ * without fixing their length. The chunk length L sets the schedule of
+ * hmm_loglik_batched: how many chunk products (work items of the persistent
+ * chunk kernels) there are, how many waves of them the GPU runs, and the size
+ * of the product tree. The tile shapes are fixed by the hardware mapping
+ * (M = 128 rows of tensor memory, N = the padded state count), so L is the
+ * schedule's free parameter. With opts->chunk_len = 0 the library uses, in
+ * this order: a chunk length the tuner stored for the call's shape, else
+ * its cost model's choice. The result depends on L only through rounding;
+ * for a fixed table it is bit-for-bit reproducible like every other call.
+ *
+ * The shape key of a stored entry is (device multiprocessor count, K,
+ * precision, n_prop, n_seg, total chain steps = sum over segments of
+ * max(0, T_s - 1), runlen_min). The table is process-wide and guarded by a
+ * lock, so every context (and thread) sees the same entries.
+ */
+
+/*
+ * The cost model's chunk length for a shape (what chunk_len = 0 uses when
+ * nothing is stored): a multiple of 64 in [64, 16384]. Host computation
+ * only; 0 for arguments out of range (K in 1..80, n_prop >= 1,
+ * steps_total >= 0, n_sms >= 1, a precision the library offers for K).
+ */
+int32_t hmm_default_chunk_len(int32_t precision, int32_t n_prop, int32_t K, int64_t steps_total,
+                              int32_t n_sms);
+
+/*
+ * The chunk lengths hmm_autotune_batched measures for a shape: the cost
+ * model's choice, its neighbours at factors 2^(j/2) (j = -3..3) and, for the
+ * tensor-core precisions, the shortest chunk length that fits each wave count
+ * within two of the model's. Ascending, distinct multiples of 64 in
+ * [64, min(16384, steps_total rounded up to 64)], at most 16. Writes at most
+ * `cap` of them to out (host) and their number to *n_out. Host computation
+ * only; HMM_EINVAL for arguments out of range (as above, cap >= 1).
+ */
+int hmm_tune_candidates(int32_t precision, int32_t n_prop, int32_t K, int64_t steps_total,
+                        int32_t n_sms, int32_t *out, int32_t cap, int32_t *n_out);
+
+/*
+ * Measures hmm_loglik_batched at every candidate chunk length for this
+ * call's shape and stores the fastest. The arguments are those of
+ * hmm_loglik_batched (device pointers, host seg_offsets), with
+ * opts->chunk_len = 0 (else HMM_EINVAL). Per candidate: one untimed call
+ * (it builds the plan and grows the workspace), then `reps` (1..100) calls
+ * between two CUDA events on `stream`; the time is their mean, without an
+ * L2 flush. A candidate whose call fails with HMM_EINVAL or HMM_ENOMEM (too
+ * many chunks for the tree, or no memory) is skipped; any other error
+ * ends the tuning and is returned. The winner is stored in the table, then
+ * evaluated once more, so out_dev (n_prop doubles) holds log L computed at
+ * the winner and hmm_last_chunk_len() returns it. *chunk_len_out and
+ * *ms_out (host, may be NULL) receive the winner and its milliseconds per
+ * call. The context keeps the largest workspace any candidate needed.
+ * Synchronises `stream`; do not call it during stream capture.
+ */
+int hmm_autotune_batched(hmm_ctx *ctx, int32_t n_prop, int32_t K, const float *pi, const float *P,
+                         const float *p_tremor, const float *mu, const float *cov, int32_t n_seg,
+                         const int64_t *seg_offsets, const float *xy, const uint8_t *tremor,
+                         const hmm_opts *opts, int32_t reps, double *out_dev, int32_t *chunk_len_out,
+                         double *ms_out, void *stream);
+
+/* The stored chunk length for a shape key, or 0 in *chunk_len if none. Host only. */
+int hmm_tune_lookup(int32_t n_sms, int32_t K, int32_t precision, int32_t n_prop, int32_t n_seg,
+                    int64_t steps_total, int32_t runlen_min, int32_t *chunk_len);
+
+/* Forget every stored chunk length. Host only. */
+int hmm_tune_clear(void);
+
+/*
+ * Write the table to a text file: a '#' comment line, then one entry per
+ * line, "n_sms K precision n_prop n_seg steps_total runlen_min chunk_len
+ * ms_per_call". HMM_EINVAL if the file cannot be written.
+ */
+int hmm_tune_save(const char *path);
+
+/*
+ * Read such a file and add its entries (an entry replaces a stored one with
+ * the same key). Blank lines and lines starting with '#' are skipped. The
+ * file is checked whole first: a malformed line or an entry out of range
+ * (chunk_len not a multiple of 64 in [64, 16384], K outside 1..80, an
+ * unknown precision, ...) or an unreadable path gives HMM_EINVAL and loads
+ * nothing.
+ */
+int hmm_tune_load(const char *path);
+
 /* ---- per-phase device timing (benchmarks) ---- */
 #define HMM_PHASE_PREP 0   /* parameter checks and constants          */
 #define HMM_PHASE_PACK 1   /* observation packing                      */

@@ -98,6 +98,16 @@ SIGNATURES = {
                                                _VP, _VP, _VP, ctypes.POINTER(hmm_opts), _VP, _VP]),
     "hmm_last_launch_count": (ctypes.c_int, [_VP]),
     "hmm_last_chunk_len": (ctypes.c_int, [_VP]),
+    "hmm_default_chunk_len": (ctypes.c_int32, [_I32, _I32, _I32, ctypes.c_int64, _I32]),
+    "hmm_tune_candidates": (ctypes.c_int, [_I32, _I32, _I32, ctypes.c_int64, _I32, _VP, _I32,
+                                           ctypes.POINTER(_I32)]),
+    "hmm_autotune_batched": (ctypes.c_int, [_VP, _I32, _I32, _VP, _VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP,
+                                            ctypes.POINTER(hmm_opts), _I32, _VP, ctypes.POINTER(_I32),
+                                            ctypes.POINTER(ctypes.c_double), _VP]),
+    "hmm_tune_lookup": (ctypes.c_int, [_I32, _I32, _I32, _I32, _I32, ctypes.c_int64, _I32, ctypes.POINTER(_I32)]),
+    "hmm_tune_clear": (ctypes.c_int, []),
+    "hmm_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "hmm_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
     "hmm_prior_default": (None, [ctypes.POINTER(hmm_prior), _I32]),
     "hmm_theta_dim": (ctypes.c_int32, [_I32]),
     "hmm_theta_to_params": (ctypes.c_int, [_I32, _I32, _VP, ctypes.POINTER(hmm_prior), _VP, _VP, _VP, _VP, _VP,
@@ -328,6 +338,30 @@ class Context:
             out.data_ptr(), _stream_ptr(stream)))
         return out
 
+    def hmm_autotune_batched(self, pi, P, p_tremor, mu, cov, seg_offsets, xy, tremor, opts=None,
+                             reps=3, out=None, stream=None):
+        """Measure the candidate chunk lengths for this shape and store the
+        fastest (later calls with chunk_len = 0 use it). Returns
+        (out: float64 [n_prop] log L at the winner, chunk length, ms per call)."""
+        n_prop, K = int(pi.shape[0]), int(pi.shape[1])
+        for t, n in ((pi, "pi"), (P, "P"), (p_tremor, "p_tremor"), (mu, "mu"), (cov, "cov")):
+            _dev(t, torch.float32, n)
+        _dev(xy, torch.float32, "xy")
+        _dev(tremor, torch.uint8, "tremor")
+        offs = np.ascontiguousarray(np.asarray(seg_offsets, dtype=np.int64))
+        if out is None:
+            out = torch.empty(n_prop, dtype=torch.float64, device=pi.device)
+        o = opts if opts is not None else make_opts()
+        T = int(offs[-1])
+        L = ctypes.c_int32(0)
+        ms = ctypes.c_double(0.0)
+        self._check(self.lib.hmm_autotune_batched(
+            self.h, n_prop, K, pi.data_ptr(), P.data_ptr(), p_tremor.data_ptr(), mu.data_ptr(),
+            cov.data_ptr(), int(offs.shape[0] - 1), offs.ctypes.data,
+            xy.data_ptr() if T else None, tremor.data_ptr() if T else None, ctypes.byref(o), int(reps),
+            out.data_ptr(), ctypes.byref(L), ctypes.byref(ms), _stream_ptr(stream)))
+        return out, int(L.value), float(ms.value)
+
     def hmm_loglik_batched_host(self, pi, P, p_tremor, mu, cov, seg_offsets, xy, tremor,
                                 opts=None, out=None, stream=None):
         """Same as hmm_loglik_batched, with host (numpy or CPU-tensor) inputs and output."""
@@ -379,6 +413,59 @@ def hmm_loglik_noalloc(pi, P, p_tremor, mu, cov, xy, tremor, out=None, stream=No
     if rc != HMM_OK:
         raise HMMError(rc, "hmm_loglik_noalloc rejected the call")
     return out
+
+
+def _prec(precision) -> int:
+    return PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+
+
+def chain_steps(seg_offsets) -> int:
+    """Total chain steps of a segment layout: sum over segments of max(0, T_s - 1)."""
+    T = np.diff(np.asarray(seg_offsets, dtype=np.int64))
+    return int(np.maximum(T - 1, 0).sum())
+
+
+def default_chunk_len(precision, n_prop, K, steps_total, n_sms) -> int:
+    """The library's cost-model chunk length for a shape (host only; 0 if out of range)."""
+    return int(load_library().hmm_default_chunk_len(_prec(precision), int(n_prop), int(K),
+                                                    int(steps_total), int(n_sms)))
+
+
+def tune_candidates(precision, n_prop, K, steps_total, n_sms) -> list[int]:
+    """The chunk lengths the tuner measures for a shape (host only)."""
+    buf = (ctypes.c_int32 * 64)()
+    n = ctypes.c_int32(0)
+    rc = load_library().hmm_tune_candidates(_prec(precision), int(n_prop), int(K), int(steps_total),
+                                            int(n_sms), buf, 64, ctypes.byref(n))
+    if rc != HMM_OK:
+        raise HMMError(rc, "hmm_tune_candidates rejected its arguments")
+    return list(buf[:n.value])
+
+
+def tune_lookup(n_sms, K, precision, n_prop, n_seg, steps_total, runlen_min=0) -> int:
+    """Stored chunk length for a shape key, 0 if none (host only)."""
+    L = ctypes.c_int32(0)
+    rc = load_library().hmm_tune_lookup(int(n_sms), int(K), _prec(precision), int(n_prop), int(n_seg),
+                                        int(steps_total), int(runlen_min), ctypes.byref(L))
+    if rc != HMM_OK:
+        raise HMMError(rc, "hmm_tune_lookup failed")
+    return int(L.value)
+
+
+def tune_clear():
+    load_library().hmm_tune_clear()
+
+
+def tune_save(path):
+    rc = load_library().hmm_tune_save(str(path).encode())
+    if rc != HMM_OK:
+        raise HMMError(rc, f"cannot write the tuning table to {path}")
+
+
+def tune_load(path):
+    rc = load_library().hmm_tune_load(str(path).encode())
+    if rc != HMM_OK:
+        raise HMMError(rc, f"cannot load a tuning table from {path}")
 
 
 def make_prior(K, **kw):

@@ -11,9 +11,11 @@
 // caller asks (hmm_status, or the _host entry point).
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -172,6 +174,112 @@ static int choose_chunk_len(int precision, int n_prop, int KP, int64_t steps_tot
     if (Li < 64) Li = 64;
     if (Li > 16384) Li = 16384;
     return (int)Li;
+}
+
+// ---- chunk-length tuning ----
+//
+// The tuner measures a handful of chunk lengths around the cost model's
+// choice and remembers the fastest per shape. The tile shapes are fixed by
+// the hardware mapping (M = 128 TMEM lanes, N = the padded state count), so
+// the chunk length is the schedule's free parameter: it sets the number of
+// work items, the waves the GPU runs them in, and the size of the tree.
+
+constexpr int TUNE_L_MAX = 16384;
+constexpr int TUNE_MAX_CANDIDATES = 16;
+
+static int round_to_win(double L) {
+    int64_t r = (int64_t)(L / OBS_WIN + 0.5) * OBS_WIN;
+    return (int)std::min<int64_t>(TUNE_L_MAX, std::max<int64_t>(OBS_WIN, r));
+}
+
+// waves of the persistent tensor-core kernel at chunk length L
+static int64_t tc_waves(int per_item, int n_prop, int64_t steps_total, int L, int n_sms) {
+    int64_t C = std::max<int64_t>(1, (steps_total + L - 1) / L);
+    int64_t items = (int64_t)n_prop * ((C + per_item - 1) / per_item);
+    return (items + n_sms - 1) / n_sms;
+}
+
+// Candidate chunk lengths: the cost model's choice, its neighbours at factors
+// 2^(j/2) (j = -3..3) and, on the tensor-core path, the shortest chunk length
+// that fits each wave count next to the model's. Ascending, distinct, multiples
+// of OBS_WIN in [OBS_WIN, min(16384, steps rounded up)].
+static std::vector<int> tune_candidates(int precision, int n_prop, int K, int64_t steps_total, int n_sms) {
+    const ConstLayout lay = make_layout(K, precision);
+    const int L0 = choose_chunk_len(precision, n_prop, lay.KP, steps_total, n_sms);
+    const int64_t Lcap = std::min<int64_t>(
+        TUNE_L_MAX, std::max<int64_t>(OBS_WIN, (steps_total + OBS_WIN - 1) / OBS_WIN * OBS_WIN));
+    std::vector<int> c;
+    auto add = [&](int L) { c.push_back((int)std::min<int64_t>(Lcap, L)); };
+    add(L0);
+    for (int j = -3; j <= 3; ++j)
+        if (j) add(round_to_win(L0 * std::pow(2.0, 0.5 * j)));
+    if (precision != HMM_PREC_FP32_SIMT) {
+        const int per_item = chunk_tc_chunks_per_item(lay.KP, precision);
+        const int64_t w0 = tc_waves(per_item, n_prop, steps_total, L0, n_sms);
+        for (int64_t w = std::max<int64_t>(1, w0 - 2); w <= w0 + 2; ++w) {
+            for (int L = OBS_WIN; L <= Lcap; L += OBS_WIN) {
+                if (tc_waves(per_item, n_prop, steps_total, L, n_sms) <= w) {
+                    add(L);
+                    break;
+                }
+            }
+        }
+    }
+    std::sort(c.begin(), c.end());
+    c.erase(std::unique(c.begin(), c.end()), c.end());
+    if ((int)c.size() > TUNE_MAX_CANDIDATES) {
+        // keep the ones nearest the model's choice (in log distance)
+        std::stable_sort(c.begin(), c.end(), [&](int a, int b) {
+            return std::fabs(std::log((double)a / L0)) < std::fabs(std::log((double)b / L0));
+        });
+        c.resize(TUNE_MAX_CANDIDATES);
+        std::sort(c.begin(), c.end());
+    }
+    return c;
+}
+
+struct TuneKey {
+    int32_t n_sms, K, precision, n_prop, n_seg, runlen_min;
+    int64_t steps;
+    bool operator==(const TuneKey &o) const {
+        return n_sms == o.n_sms && K == o.K && precision == o.precision && n_prop == o.n_prop &&
+               n_seg == o.n_seg && runlen_min == o.runlen_min && steps == o.steps;
+    }
+};
+
+struct TuneEntry {
+    TuneKey key;
+    int32_t L;
+    double ms;
+};
+
+// process-wide table of tuned chunk lengths
+static std::mutex g_tune_mu;
+static std::vector<TuneEntry> g_tune;
+
+static int tune_get(const TuneKey &k) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const TuneEntry &t : g_tune)
+        if (t.key == k) return t.L;
+    return 0;
+}
+
+static void tune_put_locked(const TuneEntry &e) {
+    for (TuneEntry &t : g_tune)
+        if (t.key == e.key) {
+            t = e;
+            return;
+        }
+    g_tune.push_back(e);
+}
+
+static bool tune_entry_valid(const TuneEntry &e) {
+    const TuneKey &k = e.key;
+    const bool prec_ok = k.precision == HMM_PREC_FP32_SIMT || k.precision == HMM_PREC_TF32 ||
+                         k.precision == HMM_PREC_BF16 || k.precision == HMM_PREC_TF32_SPLIT;
+    return k.n_sms > 0 && k.K >= 1 && k.K <= 80 && prec_ok && k.n_prop >= 1 && k.n_seg >= 1 &&
+           k.runlen_min >= 0 && k.runlen_min <= 16384 && k.steps >= 0 && e.L >= OBS_WIN &&
+           e.L <= TUNE_L_MAX && e.L % OBS_WIN == 0 && e.ms >= 0.0;
 }
 
 static void build_plan(Plan &pl, int K, int n_prop, int n_seg, const int64_t *offs, int precision,
@@ -456,7 +564,13 @@ int hmm_loglik_batched(hmm_ctx *c, int32_t n_prop, int32_t K, const float *pi, c
     int64_t steps_total = 0;
     for (int s = 0; s < n_seg; ++s) steps_total += std::max<int64_t>(0, offs[s + 1] - offs[s] - 1);
     if (!c->n_sms) cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, c->device);
-    int L = opts.chunk_len ? opts.chunk_len : choose_chunk_len(prec, n_prop, lay.KP, steps_total, c->n_sms);
+    int L = opts.chunk_len;
+    if (!L) {
+        // a tuned chunk length for this shape if the tuner stored one, else the cost model's
+        const TuneKey key{c->n_sms, K, prec, n_prop, n_seg, min_run, steps_total};
+        L = tune_get(key);
+        if (!L) L = choose_chunk_len(prec, n_prop, lay.KP, steps_total, c->n_sms);
+    }
     if (!plan_matches(c->plan, K, n_prop, n_seg, offs, prec, L)) {
         build_plan(c->plan, K, n_prop, n_seg, offs, prec, L);
         if (c->plan.n_levels + 1 > MAX_LEVELS) {
@@ -681,6 +795,184 @@ int hmm_loglik_batched_host(hmm_ctx *c, int32_t n_prop, int32_t K, const float *
     e = cudaMemcpyAsync(out_host, dout, 8 * (size_t)n_prop, cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
     return hmm_status(c, stream);
+}
+
+
+// ---- chunk-length tuning (see the header) ----
+
+int32_t hmm_default_chunk_len(int32_t precision, int32_t n_prop, int32_t K, int64_t steps_total, int32_t n_sms) {
+    if (K < 1 || K > 80 || n_prop < 1 || steps_total < 0 || n_sms < 1) return 0;
+    if (precision != HMM_PREC_FP32_SIMT && !chunk_tc_supported(K, precision)) return 0;
+    return choose_chunk_len(precision, n_prop, make_layout(K, precision).KP, steps_total, n_sms);
+}
+
+int hmm_tune_candidates(int32_t precision, int32_t n_prop, int32_t K, int64_t steps_total, int32_t n_sms,
+                        int32_t *out, int32_t cap, int32_t *n_out) {
+    if (!out || !n_out || cap < 1 || K < 1 || K > 80 || n_prop < 1 || steps_total < 0 || n_sms < 1)
+        return HMM_EINVAL;
+    if (precision != HMM_PREC_FP32_SIMT && !chunk_tc_supported(K, precision)) return HMM_EINVAL;
+    const std::vector<int> c = tune_candidates(precision, n_prop, K, steps_total, n_sms);
+    const int n = std::min<int>(cap, (int)c.size());
+    for (int i = 0; i < n; ++i) out[i] = c[i];
+    *n_out = n;
+    return HMM_OK;
+}
+
+int hmm_autotune_batched(hmm_ctx *c, int32_t n_prop, int32_t K, const float *pi, const float *P,
+                         const float *p, const float *mu, const float *cov, int32_t n_seg,
+                         const int64_t *offs, const float *xy, const uint8_t *tremor,
+                         const hmm_opts *opts_in, int32_t reps, double *out, int32_t *chunk_len_out,
+                         double *ms_out, void *stream) {
+    if (!c) return HMM_EINVAL;
+    hmm_opts opts;
+    if (opts_in) opts = *opts_in; else hmm_opts_default(&opts);
+    if (opts.chunk_len != 0) return fail(c, HMM_EINVAL, "autotuning needs opts->chunk_len = 0");
+    if (reps < 1 || reps > 100) return fail(c, HMM_EINVAL, "reps=%d outside 1..100", reps);
+    if (K < 1 || K > 80 || n_prop < 1 || n_seg < 1 || !offs)
+        return fail(c, HMM_EINVAL, "bad shape arguments");
+    if (opts.precision != HMM_PREC_FP32_SIMT && !chunk_tc_supported(K, opts.precision))
+        return fail(c, HMM_EUNSUPPORTED, "tensor-core path does not support K=%d precision %d", K, opts.precision);
+    if (offs[0] != 0) return fail(c, HMM_EINVAL, "seg_offsets[0] must be 0");
+    int64_t steps_total = 0;
+    for (int s = 0; s < n_seg; ++s) {
+        if (offs[s + 1] < offs[s]) return fail(c, HMM_EINVAL, "seg_offsets must be non-decreasing");
+        steps_total += std::max<int64_t>(0, offs[s + 1] - offs[s] - 1);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    if (!c->n_sms) cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, c->device);
+    const std::vector<int> cand = tune_candidates(opts.precision, n_prop, K, steps_total, c->n_sms);
+
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(c, e, "cudaEventCreate");
+    }
+    // the tuner's own calls stay out of the phase profile
+    const bool prof_was = c->prof_on;
+    c->prof_on = false;
+    int best_L = 0, rc = HMM_OK, last_rc = HMM_OK;
+    double best_ms = 0.0;
+    for (int L : cand) {
+        hmm_opts o = opts;
+        o.chunk_len = L;
+        // warm-up: builds the plan and grows the workspace
+        rc = hmm_loglik_batched(c, n_prop, K, pi, P, p, mu, cov, n_seg, offs, xy, tremor, &o, out, stream);
+        if (rc == HMM_EINVAL || rc == HMM_ENOMEM) {
+            // this chunk length does not fit (tree depth, memory): try the others
+            last_rc = rc;
+            rc = HMM_OK;
+            continue;
+        }
+        if (rc) break;
+        e = cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && e == cudaSuccess && rc == HMM_OK; ++r)
+            rc = hmm_loglik_batched(c, n_prop, K, pi, P, p, mu, cov, n_seg, offs, xy, tremor, &o, out, stream);
+        if (rc) break;
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(c, e, "tuning events");
+            break;
+        }
+        const double per = (double)ms / reps;
+        if (!best_L || per < best_ms) {
+            best_L = L;
+            best_ms = per;
+        }
+    }
+    c->prof_on = prof_was;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (!best_L) return fail(c, last_rc ? last_rc : HMM_EINVAL, "no candidate chunk length could be evaluated");
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_put_locked(TuneEntry{TuneKey{c->n_sms, K, opts.precision, n_prop, n_seg, opts.runlen_min, steps_total},
+                                  best_L, best_ms});
+    }
+    // leave the caller's output and the context's plan at the winner
+    hmm_opts o = opts;
+    o.chunk_len = best_L;
+    rc = hmm_loglik_batched(c, n_prop, K, pi, P, p, mu, cov, n_seg, offs, xy, tremor, &o, out, stream);
+    if (rc) return rc;
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+    if (chunk_len_out) *chunk_len_out = best_L;
+    if (ms_out) *ms_out = best_ms;
+    return HMM_OK;
+}
+
+int hmm_tune_lookup(int32_t n_sms, int32_t K, int32_t precision, int32_t n_prop, int32_t n_seg,
+                    int64_t steps_total, int32_t runlen_min, int32_t *chunk_len) {
+    if (!chunk_len) return HMM_EINVAL;
+    *chunk_len = tune_get(TuneKey{n_sms, K, precision, n_prop, n_seg, runlen_min, steps_total});
+    return HMM_OK;
+}
+
+int hmm_tune_clear(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.clear();
+    return HMM_OK;
+}
+
+int hmm_tune_save(const char *path) {
+    if (!path) return HMM_EINVAL;
+    std::vector<TuneEntry> snap;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        snap = g_tune;
+    }
+    FILE *f = fopen(path, "w");
+    if (!f) return HMM_EINVAL;
+    bool ok = fprintf(f, "# hmm_gb300 tuned chunk lengths: n_sms K precision n_prop n_seg steps_total "
+                         "runlen_min chunk_len ms_per_call\n") > 0;
+    for (const TuneEntry &t : snap)
+        ok = ok && fprintf(f, "%d %d %d %d %d %lld %d %d %.6f\n", t.key.n_sms, t.key.K, t.key.precision,
+                           t.key.n_prop, t.key.n_seg, (long long)t.key.steps, t.key.runlen_min, t.L, t.ms) > 0;
+    ok = (fclose(f) == 0) && ok;
+    return ok ? HMM_OK : HMM_EINVAL;
+}
+
+int hmm_tune_load(const char *path) {
+    if (!path) return HMM_EINVAL;
+    FILE *f = fopen(path, "r");
+    if (!f) return HMM_EINVAL;
+    std::vector<TuneEntry> got;
+    char line[512];
+    bool ok = true;
+    while (ok && fgets(line, sizeof(line), f)) {
+        const size_t n = strlen(line);
+        if (n == sizeof(line) - 1 && line[n - 1] != '\n') {  // over-long line
+            ok = false;
+            break;
+        }
+        const char *q = line;
+        while (*q == ' ' || *q == '\t') ++q;
+        if (*q == '#' || *q == '\n' || *q == '\r' || *q == '\0') continue;
+        TuneEntry t{};
+        long long steps = 0;
+        int used = 0;
+        const int m = sscanf(q, "%d %d %d %d %d %lld %d %d %lf %n", &t.key.n_sms, &t.key.K, &t.key.precision,
+                             &t.key.n_prop, &t.key.n_seg, &steps, &t.key.runlen_min, &t.L, &t.ms, &used);
+        t.key.steps = steps;
+        if (m != 9 || q[used] != '\0' || !tune_entry_valid(t)) {
+            ok = false;
+            break;
+        }
+        got.push_back(t);
+    }
+    if (ferror(f)) ok = false;
+    fclose(f);
+    if (!ok) return HMM_EINVAL;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const TuneEntry &t : got) tune_put_locked(t);
+    return HMM_OK;
 }
 
 }  // extern "C"
