@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--T", type=int, default=1 << 20)
     ap.add_argument("--n-prop", type=int, default=256)
     ap.add_argument("--chunk-len", type=int, default=0)
+    ap.add_argument("--autotune", action="store_true",
+                    help="measure the candidate chunk lengths first (hmm_autotune_batched) and run at the fastest")
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -347,6 +349,17 @@ def main():
     def step():
         ctx.hmm_loglik_batched(*dev, offs, xy, fl, opts=opts, out=out)
 
+    tuned = None
+    if args.autotune and args.chunk_len == 0:
+        # untimed: the tuner stores the fastest chunk length for this shape and
+        # the automatic choice (chunk_len = 0) in the timed steps uses it
+        _, tL, tms = ctx.hmm_autotune_batched(*dev, offs, xy, fl, opts=opts, reps=3, out=out)
+        tuned = {"chunk_len": tL, "ms_per_call": tms,
+                 "candidates": api.tune_candidates(args.precision, args.n_prop, args.K, steps_per_eval,
+                                                   torch.cuda.get_device_properties(local).multi_processor_count),
+                 "model_choice": api.default_chunk_len(args.precision, args.n_prop, args.K, steps_per_eval,
+                                                       torch.cuda.get_device_properties(local).multi_processor_count)}
+
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
@@ -403,12 +416,15 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {**workload_config(args, len(offs) - 1),
                    "precision": args.precision, "chunk_len": L,
-                   "l2": "flushed between timed steps (256 MiB write)"},
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "chunk_len_source": "autotuned" if tuned else ("fixed" if args.chunk_len else "cost model")},
         "roofline": roof,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "status": status,
     }
+    if tuned:
+        result["autotune"] = tuned
 
     # plain GPU (FP32-SIMT chunk products) on the same workload, fewer proposals
     if not args.no_plain and args.precision != "fp32":
