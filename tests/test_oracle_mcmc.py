@@ -146,3 +146,18 @@ def test_mean_outside_box_has_zero_prior():
     th[o] = 400.0  # x of state 0 beyond the 300 km box
     _, lp = oracle.theta_to_params(th, K, prior)
     assert lp == -math.inf
+
+
+def test_box_edges():
+    # each side of the box [0, 300] x [0, 150] km bounds its own coordinate only
+    K = 3
+    rng = np.random.default_rng(10)
+    prior = oracle.default_prior(K)
+    o = K * (K - 1) + (K - 1) + K
+    for x, y, inside in ((299.0, 149.0, True), (1.0, 1.0, True), (200.0, 100.0, True),
+                         (301.0, 75.0, False), (-1.0, 75.0, False), (150.0, 151.0, False),
+                         (150.0, -1.0, False)):
+        th = _random_theta(K, rng)
+        th[o], th[o + 1] = x, y
+        _, lp = oracle.theta_to_params(th, K, prior)
+        assert math.isfinite(lp) == inside, (x, y, lp)
