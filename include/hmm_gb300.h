@@ -89,9 +89,9 @@ typedef struct {
 typedef struct {
     int32_t precision;    /* HMM_PREC_*                                           */
     int32_t init_mode;    /* HMM_INIT_*                                           */
-    int32_t chunk_len;    /* steps per chunk product; 0 = chosen by the library   */
+    int32_t chunk_len;    /* steps per chunk product (multiple of 64); 0 = tuned or cost model (below) */
     int32_t renorm_every; /* per-row power-of-two renormalisation interval; 0 = 4 */
-    int32_t recheck_fp32; /* batched: re-evaluate flagged proposals in FP32-SIMT   */
+    int32_t recheck_fp32; /* samplers only (see hmm_sampler_create); ignored here  */
     int32_t runlen_min;   /* run-length shortcut, FP32-SIMT only; 0 = off (below)  */
     int32_t reserved[2];  /* must be 0                                             */
 } hmm_opts;
