@@ -81,3 +81,58 @@ def test_host_argument_checks_without_gpu(lib):
                                 None, None, None) == api.HMM_EINVAL
     assert L.hmm_status(None, None) == api.HMM_EINVAL
     assert L.hmm_destroy(None) == api.HMM_OK
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include "hmm_gb300.h"
+
+int main(void) {
+    hmm_opts o;
+    hmm_prior pr;
+    int32_t cand[32], n = 0;
+    hmm_opts_default(&o);
+    hmm_prior_default(&pr, 16);
+    if (hmm_tune_candidates(HMM_PREC_TF32, 256, 32, (1 << 20) - 1, 152, cand, 32, &n) != HMM_OK) return 2;
+    printf("%d %d %d %d\n", o.precision, o.chunk_len, o.renorm_every, (int)hmm_theta_dim(16));
+    printf("%.6f %.6f %.6f\n", pr.alpha_P, pr.iw_df, pr.box[1]);
+    printf("%d", (int)hmm_default_chunk_len(HMM_PREC_TF32, 256, 32, (1 << 20) - 1, 152));
+    for (int i = 0; i < n; ++i) printf(" %d", cand[i]);
+    printf("\n");
+    /* no context: rejected before any device call */
+    printf("%d %d\n", hmm_loglik(NULL, NULL, NULL, NULL, NULL, NULL), hmm_destroy(NULL));
+    return 0;
+}
+"""
+
+
+def test_plain_c_client(lib, tmp_path):
+    """The header is plain C99: a C program includes it, links the library
+    (no torch, no C++), and its host-only calls agree with the binding."""
+    import shutil
+    import subprocess
+    from paper_2003_03508_gb300 import api, build
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    so = build.build()
+    cuda_lib = Path(build.nvcc()).resolve().parent.parent / "lib64"
+    if not any(cuda_lib.glob("libcudart.so*")):
+        pytest.skip(f"no libcudart under {cuda_lib}")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", f"-I{ROOT / 'include'}",
+                        str(src), "-o", str(exe), str(so), f"-L{cuda_lib}", "-lcudart",
+                        f"-Wl,-rpath,{so.parent}:{cuda_lib}"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    l1, l2, l3, l4 = out.stdout.strip().splitlines()
+    assert l1.split() == [str(api.HMM_PREC_FP32_SIMT), "0", "0", str(api.theta_dim(16))]
+    a, df, x1 = map(float, l2.split())
+    assert abs(a - 0.01) < 1e-7 and df == 16.0 and x1 == 300.0
+    vals = [int(v) for v in l3.split()]
+    assert vals[0] == api.default_chunk_len("tf32", 256, 32, (1 << 20) - 1, 152)
+    assert vals[1:] == api.tune_candidates("tf32", 256, 32, (1 << 20) - 1, 152)
+    assert l4.split() == [str(api.HMM_EINVAL), str(api.HMM_OK)]
