@@ -26,8 +26,9 @@ import numpy as np
 
 def loglik_gradient(pi, P, p, mu, cov, st, init_mode: int = 0):
     """d log L / d (pi, P, p_tremor, mu, cov) as float64 arrays of the
-    parameters' shapes, from the statistics dict `st` (see oracle-free
-    layout: N [K, K], G0, Gs, Gr, Sx, Sy, Sxx, Sxy, Syy [K])."""
+    parameters' shapes, from the statistics dict `st` that
+    Context.hmm_expected_stats returns (N [K, K]; G0, Gs, Gr, Sx, Sy, Sxx,
+    Sxy, Syy [K])."""
     pi, P, p, mu, cov = (np.asarray(a, dtype=np.float64) for a in (pi, P, p, mu, cov))
     K = pi.shape[0]
     N = st["N"]
