@@ -4,6 +4,7 @@ CPU-only: these entry points do no device work, so they run without a GPU
 (the library only has to load). The measuring part, hmm_autotune_batched,
 is covered by tests/test_gpu_tune.py.
 """
+import numpy as np
 import pytest
 
 api = pytest.importorskip("paper_2003_03508_gb300.api")
@@ -130,3 +131,26 @@ def test_table_unreadable_and_unwritable_paths(tmp_path):
 def test_chain_steps():
     assert api.chain_steps([0, 10]) == 9
     assert api.chain_steps([0, 0, 1, 5]) == 3
+
+
+def test_table_load_survives_random_text(tmp_path):
+    # arbitrary bytes never crash the loader: the file is either rejected
+    # whole or (blank/comment-only) adds nothing
+    rng = np.random.default_rng(0)
+    alphabet = np.array(list(b"0123456789 -+.eE#x\t\n\r") + [0, 255, 10], dtype=np.uint8)
+    for i in range(200):
+        n = int(rng.integers(0, 300))
+        data = bytes(rng.choice(alphabet, size=n)) if i % 2 else bytes(rng.integers(0, 256, size=n, dtype=np.uint8))
+        f = tmp_path / f"r{i}.txt"
+        f.write_bytes(data)
+        try:
+            api.tune_load(f)
+        except api.HMMError:
+            pass
+    # a very long line is rejected, not truncated into a valid entry
+    long_line = f"{SMS} 32 1 256 1 1048575 0 4096 " + "1" * 600 + "\n"
+    f = tmp_path / "long.txt"
+    f.write_text(long_line)
+    with pytest.raises(api.HMMError):
+        api.tune_load(f)
+    api.tune_clear()
