@@ -1,10 +1,11 @@
 """Replays the tensor-core kernels' rounding model in numpy at full size and
 prints each precision's log-likelihood error against the FP64 oracle.
 
-    python tests/replay_precision.py [n_proposals]     (about 5 minutes at 16)
+    python tests/replay_precision.py [n_proposals] [--sparse]   (about 5 minutes at 16)
 
 Workload: the batched benchmark's inputs (K = 32, T = 2^20, proposals
-0..n-1 of seed 3). For every proposal the forward vector is advanced as the
+0..n-1 of seed 3), or with --sparse its sparse-tremor workload (seed 103,
+tremor probabilities in synth.SPARSE_P_RANGE). For every proposal the forward vector is advanced as the
 kernels advance each row of a chunk product: the operand rounded every step
 (TF32: half-ulp add on the bit pattern, low 13 bits cleared; BF16: round to
 nearest even; or truncation), P rounded once as hi (+ lo), FP32 products
@@ -71,8 +72,11 @@ def replay(d, n, rnd_v, rnd_p, split, factor=1.0, block=4096):
     return logL + np.log(v.sum(axis=1))
 
 
-def main(n=16):
-    d = synth.batched_inputs(K=32, T=1 << 20, n_prop=max(n, 1), seed=3)
+def main(n=16, sparse=False):
+    if sparse:
+        d = synth.batched_inputs(K=32, T=1 << 20, n_prop=max(n, 1), seed=103, sparse=True)
+    else:
+        d = synth.batched_inputs(K=32, T=1 << 20, n_prop=max(n, 1), seed=3)
     sub = type(d["params"])(*(a[:n] for a in d["params"].as_tuple()))
     ref = oracle.loglik_batched(sub, d["xy"], d["tremor"], d["offsets"], n_threads=8)
     f = 1.0 / (1.0 - pm.TRUNC_MEAN_LOSS)
@@ -90,4 +94,5 @@ def main(n=16):
 
 
 if __name__ == "__main__":
-    main(int(sys.argv[1]) if len(sys.argv) > 1 else 16)
+    args = [a for a in sys.argv[1:] if not a.startswith("--")]
+    main(int(args[0]) if args else 16, sparse="--sparse" in sys.argv)
