@@ -35,7 +35,10 @@ MLP_PINS = (
     ml.test_forward_matches_numpy,
     ml.test_gradient_matches_finite_differences,
     ml.test_loss_is_negative_log_density_without_constants,
-    ml.test_adam_step_rule,
+    ml.test_adam_first_step_moves_lr_against_the_gradient_sign,
+    ml.test_adam_constant_gradient_moves_lr_per_step,
+    ml.test_adam_is_invariant_to_gradient_scale,
+    ml.test_adam_reaches_the_minimiser_of_a_separable_quadratic,
 )
 
 MCMC_MUTANTS = {
@@ -72,6 +75,12 @@ MLP_MUTANTS = {
     "adam_bias_correction_dropped": ("double mh = m[i] / (1.0 - pow(b1, t));", "double mh = m[i];"),
     "adam_second_moment": ("v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];",
                            "v[i] = b2 * v[i] + (1.0 - b2) * fabs(g[i]);"),
+    "adam_second_bias_correction_dropped": ("double vh = v[i] / (1.0 - pow(b2, t));", "double vh = v[i];"),
+    "adam_sign": ("p[i] -= lr * mh / (sqrt(vh) + eps);", "p[i] += lr * mh / (sqrt(vh) + eps);"),
+    "adam_eps_inside_sqrt": ("p[i] -= lr * mh / (sqrt(vh) + eps);", "p[i] -= lr * mh / sqrt(vh + eps);"),
+    "adam_betas_swapped": ("m[i] = b1 * m[i] + (1.0 - b1) * g[i];", "m[i] = b2 * m[i] + (1.0 - b2) * g[i];"),
+    "adam_first_moment_lagged": ("double mh = m[i] / (1.0 - pow(b1, t));",
+                                 "double mh = m[i] / (1.0 - pow(b1, t + 1));"),
 }
 
 
