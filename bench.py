@@ -488,7 +488,9 @@ def main():
         mopts = api.make_opts(precision="tf32", recheck_fp32=1)
         result["mcmc"] = chains.rw_vs_learned(K=args.mcmc_K, T=args.mcmc_T, chains=args.mcmc_chains,
                                               seed=args.seed, n_measure=args.mcmc_iters, opts=mopts)
-        result["mcmc"]["likelihood"] = "tf32 tensor cores, accepted proposals rechecked in fp32"
+        result["mcmc"]["likelihood"] = ("tf32 tensor cores for every Metropolis-Hastings ratio; the chains' "
+                                        "current states (their last accepted proposals) re-evaluated in fp32 "
+                                        "at the end of each call into a separate report")
 
     if rank == 0 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1

@@ -379,11 +379,14 @@ typedef struct hmm_sampler hmm_sampler;
  * standard deviations (theta' = theta + step * N(0, I)); seed keys the
  * Philox4x32-10 counter-based generator. The observations (device, as for
  * hmm_loglik_batched; seg_offsets is a host array and is copied) must stay
- * valid while the sampler lives. opts selects the likelihood precision; with
- * opts->recheck_fp32 != 0 and a tensor-core precision, every hmm_mcmc_step
- * call ends by re-evaluating the current states with FP32-SIMT chunk
- * products, so the stored log likelihoods are FP32 ones. The sampler owns
- * its device state and two private contexts on `device`.
+ * valid while the sampler lives. opts selects the likelihood precision the
+ * Metropolis-Hastings rule works in; every acceptance ratio compares two
+ * values of that one precision. With opts->recheck_fp32 != 0 and a
+ * tensor-core precision, every hmm_mcmc_step call ends by re-evaluating the
+ * chains' current states (the proposals they last accepted) with FP32-SIMT
+ * chunk products into a separate FP32 report (hmm_sampler_fp32_report); the
+ * stored values the chains compare are not replaced. The sampler owns its
+ * device state and two private contexts on `device`.
  */
 int hmm_sampler_create(hmm_sampler **sampler, int device, int32_t n_chains, int32_t K,
                        const hmm_prior *prior, const float *theta0, const float *step, uint64_t seed,
@@ -393,10 +396,12 @@ int hmm_sampler_create(hmm_sampler **sampler, int device, int32_t n_chains, int3
 int hmm_sampler_destroy(hmm_sampler *sampler);
 
 /*
- * n_iter iterations of every chain: propose, evaluate the batched likelihood
- * of all proposals, accept or reject (log u < log posterior ratio, u from
- * Philox). After the first iteration the sampler runs each iteration as one
- * CUDA graph replay. trace_logpost (device [n_iter][n_chains] float) and
+ * n_iter iterations of every chain (Section "Monte Carlo Markov Chains": a
+ * proposal is accepted with probability min(1, ratio of likelihood x prior),
+ * times the proposal's Hastings factor where it is not symmetric): propose,
+ * evaluate the batched likelihood of all proposals, accept or reject
+ * (log u < log posterior ratio, u from Philox). After the first iteration the
+ * sampler runs each iteration as one CUDA graph replay. trace_logpost (device [n_iter][n_chains] float) and
  * trace_theta (device [n_iter][n_chains][D] float) receive the state after
  * each iteration when not NULL. Asynchronous on `stream`, except for a short
  * synchronisation at the start of the call.
@@ -404,10 +409,44 @@ int hmm_sampler_destroy(hmm_sampler *sampler);
 int hmm_mcmc_step(hmm_sampler *sampler, int32_t n_iter, float *trace_logpost, float *trace_theta,
                   void *stream);
 
-/* Re-evaluate every chain's current state with FP32-SIMT chunk products
- * (the reported log likelihood becomes the FP32 one); *max_abs_change_dev
- * (device double, may be NULL) receives the largest change. */
-int hmm_sampler_recheck(hmm_sampler *sampler, double *max_abs_change_dev, void *stream);
+/*
+ * FP32 recheck of the accepted proposals: re-evaluates every chain's current
+ * state (its last accepted proposal) with FP32-SIMT chunk products now, on
+ * `stream`. loglik_fp32_out (device, n_chains doubles) receives those log
+ * likelihoods and *max_abs_diff_dev (device double) the largest
+ * |FP32 value - stored value| over the chains; either may be NULL. The
+ * stored values (hmm_sampler_state's log likelihood and log posterior) are
+ * not changed, so later acceptance ratios stay in the sampler's precision.
+ */
+int hmm_sampler_recheck(hmm_sampler *sampler, double *loglik_fp32_out, double *max_abs_diff_dev, void *stream);
+
+/*
+ * The most recent FP32 recheck (the automatic one at the end of an
+ * hmm_mcmc_step call with opts->recheck_fp32, or hmm_sampler_recheck), copied
+ * without evaluating anything; NaN before the first recheck. Arguments as for
+ * hmm_sampler_recheck.
+ */
+int hmm_sampler_fp32_report(hmm_sampler *sampler, double *loglik_fp32_out, double *max_abs_diff_dev,
+                            void *stream);
+
+/*
+ * Checkpoints. hmm_sampler_save writes, after the sampler's queued work and
+ * `stream` have finished, everything the chains' future depends on to the
+ * file `path`: the states theta, their log posteriors, log likelihoods and
+ * log priors, acceptance counts, the proposal step sizes, the Philox seed and
+ * iteration counter, the proposal kind, the t-walk's second points, the FP32
+ * report and, with the learned proposal, the network's parameters,
+ * standardisation, scale, lam and drift. hmm_sampler_load restores such a
+ * file into a sampler created with the same n_chains, K and observation
+ * layout (n_seg and total length are checked; the data themselves are the
+ * caller's); with the learned proposal the sampler must already use a
+ * network of the saved shape, which is overwritten. After a load the sampler
+ * continues bit for bit as the saved one would have. HMM_EINVAL for an
+ * unreadable or unwritable path, a file that is not a checkpoint, or a
+ * mismatch; both synchronise `stream`.
+ */
+int hmm_sampler_save(hmm_sampler *sampler, const char *path, void *stream);
+int hmm_sampler_load(hmm_sampler *sampler, const char *path, void *stream);
 
 /* Copy the current states: theta [n_chains][D] (float), log posterior,
  * log likelihood (double), accepted-proposal counts (uint64); all device
@@ -515,12 +554,19 @@ int hmm_sampler_set_proposal(hmm_sampler *sampler, int32_t kind, hmm_mlp *mlp);
  * when the library is loaded and held by every GPU that loads it until the
  * process exits. The caller passes inputs and output as for hmm_loglik.
  *
- * Computes what hmm_loglik computes with default options (FP32-SIMT chunk
- * products, emit-first convention, chunk length 1024, renormalisation every
- * 4 steps), for 1 <= K <= HMM_NOALLOC_MAX_K and 0 <= T <= HMM_NOALLOC_MAX_T;
- * anything larger is rejected with HMM_EINVAL before any work is queued.
- * out_dev: device pointer to one double. Invalid parameter data (checked on
- * the device) gives NaN; a true zero likelihood gives -INFINITY.
+ * Computes what hmm_loglik computes with precision HMM_PREC_FP32_SIMT,
+ * emit-first convention, chunk_len 1024 and renorm_every 4 (so it agrees
+ * with hmm_loglik's default options, whose chunk length is chosen
+ * automatically, within the FP32 tolerance, not bit for bit), for
+ * 1 <= K <= HMM_NOALLOC_MAX_K and 0 <= T <= HMM_NOALLOC_MAX_T; anything
+ * larger is rejected with HMM_EINVAL before any work is queued.
+ * out_dev: device pointer to one double. A true zero likelihood gives
+ * -INFINITY. There is no context whose status word hmm_status() could
+ * read, so the call's last kernel reads the status on `stream` and writes
+ * NaN to out_dev when the device found invalid parameter data, a flagged
+ * observation with non-finite xy, a value outside the representable range
+ * (an emission below 2^-65536 of the step's best state) or an expired wait:
+ * a NaN result is this call's device-side error report.
  *
  * The first call on each device looks the scratch address up (with that
  * device current), so make it before any stream capture. Every call reuses

@@ -117,7 +117,10 @@ SIGNATURES = {
                                           ctypes.POINTER(hmm_opts), _VP]),
     "hmm_sampler_destroy": (ctypes.c_int, [_VP]),
     "hmm_mcmc_step": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP]),
-    "hmm_sampler_recheck": (ctypes.c_int, [_VP, _VP, _VP]),
+    "hmm_sampler_recheck": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "hmm_sampler_fp32_report": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "hmm_sampler_save": (ctypes.c_int, [_VP, ctypes.c_char_p, _VP]),
+    "hmm_sampler_load": (ctypes.c_int, [_VP, ctypes.c_char_p, _VP]),
     "hmm_sampler_state": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "hmm_sampler_launches_per_iter": (ctypes.c_int, [_VP]),
     "hmm_sampler_graph_active": (ctypes.c_int, [_VP]),
@@ -554,11 +557,36 @@ class Sampler:
         return lp, th
 
     def recheck(self, stream=None):
+        """FP32-SIMT log likelihoods of the current states (float64 [C]) and
+        the largest difference from the stored values (float64 [1]); the
+        stored values are left as they are."""
+        ll = torch.empty(self.C, dtype=torch.float64, device="cuda")
         d = torch.empty(1, dtype=torch.float64, device="cuda")
-        rc = self.lib.hmm_sampler_recheck(self.h, d.data_ptr(), _stream_ptr(stream))
+        rc = self.lib.hmm_sampler_recheck(self.h, ll.data_ptr(), d.data_ptr(), _stream_ptr(stream))
         if rc != HMM_OK:
             raise HMMError(rc, "hmm_sampler_recheck failed")
-        return d
+        return ll, d
+
+    def fp32_report(self, stream=None):
+        """The most recent FP32 recheck (values [C], largest difference [1]); NaN before any."""
+        ll = torch.empty(self.C, dtype=torch.float64, device="cuda")
+        d = torch.empty(1, dtype=torch.float64, device="cuda")
+        rc = self.lib.hmm_sampler_fp32_report(self.h, ll.data_ptr(), d.data_ptr(), _stream_ptr(stream))
+        if rc != HMM_OK:
+            raise HMMError(rc, "hmm_sampler_fp32_report failed")
+        return ll, d
+
+    def save(self, path, stream=None):
+        """Write a checkpoint of the sampler's state to `path`."""
+        rc = self.lib.hmm_sampler_save(self.h, str(path).encode(), _stream_ptr(stream))
+        if rc != HMM_OK:
+            raise HMMError(rc, f"hmm_sampler_save({path}) failed")
+
+    def load(self, path, stream=None):
+        """Restore a checkpoint written by save() for the same chains and data."""
+        rc = self.lib.hmm_sampler_load(self.h, str(path).encode(), _stream_ptr(stream))
+        if rc != HMM_OK:
+            raise HMMError(rc, f"hmm_sampler_load({path}) failed")
 
     def state(self, stream=None):
         th = torch.empty(self.C, self.D, device="cuda")

@@ -32,8 +32,10 @@
 // kept in device memory. After a first, ordinary iteration the sampler
 // captures one iteration in a CUDA graph and replays it.
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "hmm_internal.cuh"
 
@@ -45,6 +47,8 @@ float mlp_lambda(const hmm_mlp *m);
 float mlp_drift(const hmm_mlp *m);
 const float *mlp_scale(const hmm_mlp *m);
 int mlp_eval(hmm_mlp *m, int B, const float *theta, float *x, float *a1, float *a2, float *out, cudaStream_t st);
+size_t mlp_state_floats(const hmm_mlp *m);
+cudaError_t mlp_state_io(hmm_mlp *m, float *host, float *lam, float *drift, bool save, cudaStream_t st);
 
 namespace mcmc {
 
@@ -501,17 +505,15 @@ __global__ void __launch_bounds__(TPB) accept_twalk_kernel(int D, uint64_t seed,
 
 __global__ void advance_kernel(Ctl *ctl) { ctl->iter += 1; }
 
-// replace the stored log likelihood of every chain by its FP32-SIMT value and
-// record the largest change
-__global__ void recheck_kernel(int C, const double *ll32, double *loglik, double *logpost, const double *logprior,
-                               double *maxdiff) {
+// largest |FP32-SIMT value - stored value| over the chains. The stored values
+// (the ones the Metropolis-Hastings rule compares) are left as they are, so
+// every acceptance ratio stays within the sampler's own precision.
+__global__ void recheck_kernel(int C, const double *ll32, const double *loglik, double *maxdiff) {
     __shared__ double red[128];
     double m = 0.0;
     for (int c = threadIdx.x; c < C; c += 128) {
         const double d = fabs(ll32[c] - loglik[c]);
         if (!isnan(d)) m = fmax(m, d);
-        loglik[c] = ll32[c];
-        logpost[c] = ll32[c] + logprior[c];
     }
     red[threadIdx.x] = m;
     __syncthreads();
@@ -712,6 +714,9 @@ int hmm_sampler_create(hmm_sampler **out, int device, int32_t n_chains, int32_t 
     e = cudaMemcpyAsync(s->theta, theta0, sizeof(float) * C * D, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->step, step, sizeof(float) * D, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->n_acc, 0, sizeof(unsigned long long) * C, st);
+    // no recheck yet: the FP32 report reads NaN (all bits set)
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->loglik32, 0xff, sizeof(double) * C, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->recheck_maxdiff, 0xff, sizeof(double), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->ctl, &c0, sizeof(Ctl), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
@@ -857,8 +862,11 @@ static int mcmc_step_own(hmm_sampler *s, int32_t n_iter, float *trace_logpost, f
     return HMM_OK;
 }
 
-// FP32-SIMT re-evaluation of every chain's current state (precision rows of
-// the batched path: the reported log likelihood becomes the FP32 one)
+// FP32-SIMT re-evaluation of every chain's current state, i.e. of the last
+// proposal each chain accepted, into the sampler's FP32 report (loglik32) and
+// the largest difference from the stored values. It never feeds back into the
+// chains: their stored log likelihoods, and so every later acceptance ratio,
+// stay in the sampler's precision.
 static int recheck(hmm_sampler *s, cudaStream_t st) {
     if (!s->lik32) {
         int dev = 0;
@@ -876,20 +884,30 @@ static int recheck(hmm_sampler *s, cudaStream_t st) {
     int rc = hmm_loglik_batched(s->lik32, C, K, s->pi, s->P, s->p, s->mu, s->cov, s->n_seg, s->offs, s->xy,
                                 s->tremor, &o, s->loglik32, st);
     if (rc) return rc;
-    recheck_kernel<<<1, 128, 0, st>>>(C, s->loglik32, s->loglik, s->logpost, s->logprior, s->recheck_maxdiff);
+    recheck_kernel<<<1, 128, 0, st>>>(C, s->loglik32, s->loglik, s->recheck_maxdiff);
     return cudaGetLastError() == cudaSuccess ? HMM_OK : HMM_ECUDA;
 }
 
-int hmm_sampler_recheck(hmm_sampler *s, double *max_abs_change_dev, void *stream) {
+static int copy_fp32_report(hmm_sampler *s, double *loglik_fp32_out, double *max_abs_diff_dev, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    if (loglik_fp32_out)
+        e = cudaMemcpyAsync(loglik_fp32_out, s->loglik32, sizeof(double) * s->C, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && max_abs_diff_dev)
+        e = cudaMemcpyAsync(max_abs_diff_dev, s->recheck_maxdiff, sizeof(double), cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? HMM_OK : HMM_ECUDA;
+}
+
+int hmm_sampler_recheck(hmm_sampler *s, double *loglik_fp32_out, double *max_abs_diff_dev, void *stream) {
     if (!s) return HMM_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     int rc = recheck(s, st);
     if (rc) return rc;
-    if (max_abs_change_dev &&
-        cudaMemcpyAsync(max_abs_change_dev, s->recheck_maxdiff, sizeof(double), cudaMemcpyDeviceToDevice, st) !=
-            cudaSuccess)
-        return HMM_ECUDA;
-    return HMM_OK;
+    return copy_fp32_report(s, loglik_fp32_out, max_abs_diff_dev, st);
+}
+
+int hmm_sampler_fp32_report(hmm_sampler *s, double *loglik_fp32_out, double *max_abs_diff_dev, void *stream) {
+    if (!s) return HMM_EINVAL;
+    return copy_fp32_report(s, loglik_fp32_out, max_abs_diff_dev, (cudaStream_t)stream);
 }
 
 int hmm_sampler_state(hmm_sampler *s, float *theta_out, double *logpost_out, double *loglik_out,
@@ -988,6 +1006,166 @@ int hmm_sampler_set_proposal(hmm_sampler *s, int32_t kind, hmm_mlp *mlp) {
     s->graph_failed = 0;
     s->kind = kind;
     s->mlp = kind == HMM_PROPOSAL_MLP ? mlp : nullptr;
+    return HMM_OK;
+}
+
+// ---- checkpoints ----
+//
+// File layout (native byte order): the 8-byte tag "HMMSMP01"; int32 C, K, D,
+// proposal kind, has second points, network d, network hidden width, n_seg;
+// int64 total observations; uint64 seed, iteration counter; float step[D];
+// float theta[C][D]; double logpost[C], loglik[C], logprior[C]; uint64
+// accepted[C]; double FP32 report[C] and its largest difference; then, with
+// second points, float theta2[C][D] and double logpost2/loglik2/logprior2[C];
+// then, for the learned proposal, the network state (parameters, mean,
+// in_scale, scale) and float lam, drift.
+
+static const char CKPT_TAG[8] = {'H', 'M', 'M', 'S', 'M', 'P', '0', '1'};
+
+struct CkptHead {
+    int32_t C, K, D, kind, has2, mlp_d, mlp_h, n_seg;
+    int64_t T_total;
+    uint64_t seed, iter;
+};
+
+namespace {
+
+struct Blob {
+    void *dev;
+    size_t bytes;
+};
+
+std::vector<Blob> ckpt_blobs(hmm_sampler *s, bool with2) {
+    const size_t C = s->C, D = s->D;
+    std::vector<Blob> b = {{s->step, sizeof(float) * D},          {s->theta, sizeof(float) * C * D},
+                           {s->logpost, sizeof(double) * C},      {s->loglik, sizeof(double) * C},
+                           {s->logprior, sizeof(double) * C},     {s->n_acc, sizeof(unsigned long long) * C},
+                           {s->loglik32, sizeof(double) * C},     {s->recheck_maxdiff, sizeof(double)}};
+    if (with2) {
+        b.push_back({s->theta2, sizeof(float) * C * D});
+        b.push_back({s->logpost2, sizeof(double) * C});
+        b.push_back({s->loglik2, sizeof(double) * C});
+        b.push_back({s->logprior2, sizeof(double) * C});
+    }
+    return b;
+}
+
+void drop_graph(hmm_sampler *s) {
+    if (s->exec) {
+        cudaGraphExecDestroy(s->exec);
+        s->exec = nullptr;
+    }
+    if (s->graph) {
+        cudaGraphDestroy(s->graph);
+        s->graph = nullptr;
+    }
+    s->graph_failed = 0;
+}
+
+}  // namespace
+
+int hmm_sampler_save(hmm_sampler *s, const char *path, void *stream) {
+    if (!s || !path) return HMM_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    // iterations replay on the sampler's own stream: the state is final after it
+    if (s->own && cudaStreamSynchronize(s->own) != cudaSuccess) return HMM_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return HMM_ECUDA;
+    CkptHead h{};
+    h.C = s->C;
+    h.K = s->K;
+    h.D = s->D;
+    h.kind = s->kind;
+    h.has2 = s->theta2 ? 1 : 0;
+    h.mlp_d = s->kind == HMM_PROPOSAL_MLP ? mlp_dim(s->mlp) : 0;
+    h.mlp_h = s->kind == HMM_PROPOSAL_MLP ? mlp_hidden(s->mlp) : 0;
+    h.n_seg = s->n_seg;
+    h.T_total = s->offs[s->n_seg];
+    h.seed = s->seed;
+    h.iter = s->iter_host;
+    std::vector<char> buf(sizeof(CKPT_TAG) + sizeof(h));
+    memcpy(buf.data(), CKPT_TAG, sizeof(CKPT_TAG));
+    memcpy(buf.data() + sizeof(CKPT_TAG), &h, sizeof(h));
+    for (const Blob &b : ckpt_blobs(s, h.has2)) {
+        const size_t o = buf.size();
+        buf.resize(o + b.bytes);
+        if (cudaMemcpyAsync(buf.data() + o, b.dev, b.bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return HMM_ECUDA;
+    }
+    if (h.kind == HMM_PROPOSAL_MLP) {
+        const size_t nf = mlp_state_floats(s->mlp);
+        const size_t o = buf.size();
+        buf.resize(o + sizeof(float) * (nf + 2));
+        float *f = reinterpret_cast<float *>(buf.data() + o);
+        if (mlp_state_io(s->mlp, f, f + nf, f + nf + 1, true, st) != cudaSuccess) return HMM_ECUDA;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) return HMM_ECUDA;
+    FILE *fp = fopen(path, "wb");
+    if (!fp) return HMM_EINVAL;
+    const bool ok = fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
+    const bool closed = fclose(fp) == 0;
+    return ok && closed ? HMM_OK : HMM_EINVAL;
+}
+
+int hmm_sampler_load(hmm_sampler *s, const char *path, void *stream) {
+    if (!s || !path) return HMM_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    FILE *fp = fopen(path, "rb");
+    if (!fp) return HMM_EINVAL;
+    std::vector<char> buf;
+    char chunk[1 << 16];
+    size_t n;
+    while ((n = fread(chunk, 1, sizeof(chunk), fp)) > 0) buf.insert(buf.end(), chunk, chunk + n);
+    fclose(fp);
+    CkptHead h{};
+    if (buf.size() < sizeof(CKPT_TAG) + sizeof(h) || memcmp(buf.data(), CKPT_TAG, sizeof(CKPT_TAG)) != 0)
+        return HMM_EINVAL;
+    memcpy(&h, buf.data() + sizeof(CKPT_TAG), sizeof(h));
+    // the sampler must have been created for the same chains and data
+    if (h.C != s->C || h.K != s->K || h.D != s->D || h.n_seg != s->n_seg || h.T_total != s->offs[s->n_seg])
+        return HMM_EINVAL;
+    if (h.kind != HMM_PROPOSAL_RW && h.kind != HMM_PROPOSAL_MLP && h.kind != HMM_PROPOSAL_TWALK) return HMM_EINVAL;
+    if (h.kind == HMM_PROPOSAL_TWALK && !h.has2) return HMM_EINVAL;
+    // the learned proposal is restored into the network the sampler uses now
+    if (h.kind == HMM_PROPOSAL_MLP &&
+        (s->kind != HMM_PROPOSAL_MLP || !s->mlp || mlp_dim(s->mlp) != h.mlp_d || mlp_hidden(s->mlp) != h.mlp_h))
+        return HMM_EINVAL;
+    size_t need = sizeof(CKPT_TAG) + sizeof(h);
+    if (h.has2 && !s->theta2) {
+        const int C = s->C, D = s->D;
+        cudaError_t e = cudaMalloc(&s->theta2, sizeof(float) * C * D);
+        if (e == cudaSuccess) e = cudaMalloc(&s->logpost2, sizeof(double) * C);
+        if (e == cudaSuccess) e = cudaMalloc(&s->loglik2, sizeof(double) * C);
+        if (e == cudaSuccess) e = cudaMalloc(&s->logprior2, sizeof(double) * C);
+        if (e == cudaSuccess) e = cudaMalloc(&s->tw_W, sizeof(double) * C);
+        if (e == cudaSuccess) e = cudaMalloc(&s->tw_side, sizeof(int) * C);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return HMM_ENOMEM;
+        }
+    }
+    const std::vector<Blob> blobs = ckpt_blobs(s, h.has2);
+    for (const Blob &b : blobs) need += b.bytes;
+    const size_t nf = h.kind == HMM_PROPOSAL_MLP ? mlp_state_floats(s->mlp) : 0;
+    if (h.kind == HMM_PROPOSAL_MLP) need += sizeof(float) * (nf + 2);
+    if (buf.size() != need) return HMM_EINVAL;
+    if (s->own && cudaStreamSynchronize(s->own) != cudaSuccess) return HMM_ECUDA;
+    size_t o = sizeof(CKPT_TAG) + sizeof(h);
+    for (const Blob &b : blobs) {
+        if (cudaMemcpyAsync(b.dev, buf.data() + o, b.bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return HMM_ECUDA;
+        o += b.bytes;
+    }
+    if (h.kind == HMM_PROPOSAL_MLP) {
+        float *f = reinterpret_cast<float *>(buf.data() + o);
+        if (mlp_state_io(s->mlp, f, f + nf, f + nf + 1, false, st) != cudaSuccess) return HMM_ECUDA;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) return HMM_ECUDA;
+    // the seed and the proposal kind are kernel arguments of the captured iteration
+    drop_graph(s);
+    s->seed = h.seed;
+    s->iter_host = h.iter;
+    s->kind = h.kind;
+    if (h.kind != HMM_PROPOSAL_MLP) s->mlp = nullptr;
     return HMM_OK;
 }
 

@@ -430,6 +430,32 @@ const float *mlp_scale(const hmm_mlp *m) { return m->scale; }
 int mlp_hidden(const hmm_mlp *m) { return m->H; }
 const float *mlp_mean(const hmm_mlp *m) { return m->mean; }
 
+// What a proposal built on the network depends on (sampler checkpoints):
+// the parameters, the input standardisation (mean, in_scale), the scale,
+// lam and the drift factor; n_params + 3d floats plus the two scalars.
+size_t mlp_state_floats(const hmm_mlp *m) { return m->n_params + 3 * (size_t)m->d; }
+
+cudaError_t mlp_state_io(hmm_mlp *m, float *host, float *lam, float *drift, bool save, cudaStream_t st) {
+    float *dev[4] = {m->params, m->mean, m->in_scale, m->scale};
+    const size_t n[4] = {m->n_params, (size_t)m->d, (size_t)m->d, (size_t)m->d};
+    cudaError_t e = cudaSuccess;
+    size_t o = 0;
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+        e = save ? cudaMemcpyAsync(host + o, dev[i], sizeof(float) * n[i], cudaMemcpyDeviceToHost, st)
+                 : cudaMemcpyAsync(dev[i], host + o, sizeof(float) * n[i], cudaMemcpyHostToDevice, st);
+        o += n[i];
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (save) {
+        *lam = m->lam;
+        *drift = m->drift;
+    } else if (e == cudaSuccess) {
+        m->lam = *lam;
+        m->drift = *drift;
+    }
+    return e;
+}
+
 // network outputs for B states into out (B x 2d) through caller-owned buffers
 // x [B][d], a1 and a2 [B][H] (their addresses stay fixed under a CUDA graph)
 int mlp_eval(hmm_mlp *m, int B, const float *theta, float *x, float *a1, float *a2, float *out, cudaStream_t st) {

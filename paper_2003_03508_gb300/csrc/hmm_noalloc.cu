@@ -18,6 +18,13 @@
 // that must start at zero are cleared on the call's stream. Calls whose work
 // overlaps on the GPU (different streams, or different host threads, without
 // ordering between them) race on the array: order them or use hmm_loglik.
+//
+// Without a context there is no hmm_status() to read the device status word,
+// so the call's last kernel reads it on the stream and turns a failed call
+// into a NaN result: invalid parameters or flagged observations (already NaN
+// from the combine), a value that left the representable range (an emission
+// below 2^-65536 of the step's best state, or a non-finite product), or a
+// bounded device wait that ran out.
 #include <algorithm>
 #include <mutex>
 
@@ -125,6 +132,11 @@ __global__ void noalloc_plan_kernel(int64_t T, int C, int n_levels, int ng0, int
     }
 }
 
+// the status word as the result: any failure bit makes log L NaN
+__global__ void noalloc_status_kernel(const unsigned *status, double *out) {
+    if (*status & (ST_EINVAL | ST_ENUMERIC | ST_ETIMEOUT)) *out = __longlong_as_double(0x7ff8000000000000LL);
+}
+
 }  // namespace
 }  // namespace hmm
 
@@ -204,6 +216,10 @@ extern "C" int hmm_loglik_noalloc(const hmm_params *prm, const hmm_obs *obs, dou
     if (e == cudaSuccess)
         e = launch_final(1, K, HMM_INIT_EMIT_FIRST, 1, segs, head, lv, lay.KP, prm->pi, prm->P, prm->p_tremor,
                          prm->mu, prm->cov, prop_bad, obs_bad, out_dev, st);
+    if (e == cudaSuccess) {
+        noalloc_status_kernel<<<1, 1, 0, st>>>(status, out_dev);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         return HMM_ECUDA;

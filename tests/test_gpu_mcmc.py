@@ -10,7 +10,10 @@
   prior: started at exact prior draws, they must keep the prior's moments.
   A wrong Jacobian or acceptance rule makes them drift.
 * One call of n iterations (a CUDA graph replay) equals n calls of one.
-* The FP32 recheck leaves FP32-SIMT log likelihoods.
+* The FP32 recheck of accepted proposals is a separate report: it matches
+  the oracle and never changes the values the acceptance rule compares.
+* A checkpoint (hmm_sampler_save/load) resumes bit for bit, for the random
+  walk, the t-walk and the learned proposal.
 """
 import math
 
@@ -223,19 +226,183 @@ def test_stored_loglik_is_the_likelihood_of_the_state(cuda_lib):
     s.close()
 
 
-def test_tf32_sampler_with_fp32_recheck(cuda_lib):
+def test_fp32_recheck_reports_and_leaves_the_chains_alone(cuda_lib):
+    """The FP32 recheck of the accepted proposals is a report: a TF32
+    sampler with it on, stepped one iteration per call (a recheck after every
+    call), moves exactly like the same sampler with it off stepped in one
+    call, so no acceptance ratio ever mixes an FP32 value with a TF32 one.
+    The stored log likelihoods stay the TF32 evaluations of the states; the
+    report holds FP32 values that match the FP64 oracle."""
     api = cuda_lib
-    K, C = 16, 16
-    s, th0, step, obs, pr = _make_sampler(api, K, C, 5, T=20000, step_scale=0.01, precision="tf32", recheck=1)
-    s.step(5)
-    assert s.graph_active
-    th, lp, ll, na = s.state()
-    (pi, P, p, mu, cov), _ = api.theta_to_params(th, K, pr)
-    ctx = api.default_context()
-    ref = ctx.hmm_loglik_batched(pi.contiguous(), P.contiguous(), p.contiguous(), mu.contiguous(),
-                                 cov.contiguous(), [0, obs.T], torch.from_numpy(obs.xy).cuda(),
-                                 torch.from_numpy(obs.tremor).cuda(), opts=api.make_opts(precision="fp32"))
+    K, C, n = 16, 16, 6
+    a, th0, step, obs, pr = _make_sampler(api, K, C, 5, T=20000, step_scale=0.01, precision="tf32", recheck=1)
+    b, *_ = _make_sampler(api, K, C, 5, T=20000, step_scale=0.01, precision="tf32", recheck=0)
+    assert torch.isnan(a.fp32_report()[0]).all()  # nothing rechecked yet
+    la = torch.cat([a.step(1, trace_logpost=True)[0] for _ in range(n)])
+    lb, _ = b.step(n, trace_logpost=True)
+    ta, lpa, lla, naa = a.state()
+    tb, lpb, llb, nab = b.state()
     torch.cuda.synchronize()
-    assert torch.all(torch.isfinite(ll))
-    assert torch.equal(ll, ref)
-    s.close()
+    assert torch.equal(la, lb) and torch.equal(ta, tb) and torch.equal(lpa, lpb) and torch.equal(lla, llb)
+    assert torch.equal(naa, nab) and naa.sum().item() > 0
+    (pi, P, p, mu, cov), _ = api.theta_to_params(ta, K, pr)
+    xy, fl = torch.from_numpy(obs.xy).cuda(), torch.from_numpy(obs.tremor).cuda()
+    ctx = api.default_context()
+    tf = ctx.hmm_loglik_batched(pi.contiguous(), P.contiguous(), p.contiguous(), mu.contiguous(),
+                                cov.contiguous(), [0, obs.T], xy, fl, opts=api.make_opts(precision="tf32"))
+    rep, dmax = a.fp32_report()
+    torch.cuda.synchronize()
+    assert torch.equal(lla, tf)  # the stored values are the sampler's own precision
+    rep = rep.cpu().numpy()
+    for c in range(C):
+        prm = tuple(t[c].cpu().numpy() for t in (pi, P, p, mu, cov))
+        o = oracle.loglik(prm, obs.xy, obs.tremor)
+        assert abs(rep[c] - o) <= 1e-6 * abs(o) + 1e-4, (c, rep[c], o)
+    assert abs(dmax.item() - np.abs(rep - lla.cpu().numpy()).max()) <= 1e-9
+    # an explicit recheck evaluates again and agrees with the automatic one
+    ll2, _ = a.recheck()
+    torch.cuda.synchronize()
+    assert np.array_equal(ll2.cpu().numpy(), rep)
+    a.close(); b.close()
+
+
+def test_tf32_decisions_use_tf32_values_on_both_sides(cuda_lib):
+    """Every accept/reject decision of a TF32 sampler with the FP32 recheck
+    on, across call boundaries, equals the Metropolis-Hastings rule replayed
+    on the host from the oracle's Philox draws, the oracle's log prior and
+    the TF32 log likelihoods of the current state and of the proposal (the
+    same batched TF32 evaluation at the same chunk length)."""
+    api = cuda_lib
+    K, C, seed, n = 4, 32, 31, 6
+    rng = np.random.default_rng(seed)
+    D = api.theta_dim(K)
+    gen = synth.random_params(K, rng)
+    obs = synth.sample_observations(gen, 4000, rng)
+    th0 = _near_truth(K, C, gen, rng, scale=0.02)
+    step = np.full(D, 0.02, np.float32)
+    o0 = K * (K - 1) + (K - 1) + K
+    step[o0:o0 + 2 * K] = 1.0
+    pr = api.make_prior(K, alpha_P=0.5)
+    xy, fl = torch.from_numpy(obs.xy).cuda(), torch.from_numpy(obs.tremor).cuda()
+    opts = api.make_opts(precision="tf32", chunk_len=256, recheck_fp32=1)
+    s = api.Sampler(K, torch.from_numpy(th0).cuda(), torch.from_numpy(step).cuda(), seed, [0, obs.T], xy, fl,
+                    prior=pr, opts=opts)
+    traces = [s.step(1, trace_theta=True)[1] for _ in range(n)]
+    torch.cuda.synchronize()
+    ctx = api.Context()
+    prior = _oprior(pr)
+
+    def tf32_loglik(thetas):
+        (pi, P, p, mu, cov), _ = api.theta_to_params(torch.from_numpy(thetas).cuda(), K, pr)
+        out = ctx.hmm_loglik_batched(pi.contiguous(), P.contiguous(), p.contiguous(), mu.contiguous(),
+                                     cov.contiguous(), [0, obs.T], xy, fl,
+                                     opts=api.make_opts(precision="tf32", chunk_len=256))
+        return out.cpu().numpy()
+
+    cur = th0.copy()
+    cur_ll = tf32_loglik(cur)
+    cur_lp = np.array([oracle.theta_to_params(cur[c].astype(np.float64), K, prior)[1] for c in range(C)])
+    n_acc = 0
+    for it in range(n):
+        props = np.empty_like(cur)
+        for c in range(C):
+            z = np.array([oracle.normal(seed, 0, c, it, d) for d in range(D)])
+            props[c] = (cur[c].astype(np.float64) + step.astype(np.float64) * z).astype(np.float32)
+        pll = tf32_loglik(props)
+        got = traces[it][0].cpu().numpy()
+        for c in range(C):
+            plp = oracle.theta_to_params(props[c].astype(np.float64), K, prior)[1]
+            u = oracle.uniform(seed, 0, c, it, 0)
+            accept = math.isfinite(plp) and math.log(u) < (pll[c] + plp) - (cur_ll[c] + cur_lp[c])
+            if accept:
+                assert np.array_equal(got[c], props[c]), (it, c)
+                cur[c], cur_ll[c], cur_lp[c] = props[c], pll[c], plp
+                n_acc += 1
+            else:
+                assert np.array_equal(got[c], cur[c]), (it, c)
+    assert 0 < n_acc < n * C
+    ctx.close(); s.close()
+
+
+def _run_pair(api, make, n1, n2, tmp_path, setup=None):
+    """Sampler A runs n1 iterations, is saved, runs n2 more; sampler B (made
+    the same way) loads the checkpoint and runs n2: both must end equal."""
+    a = make()
+    b = make()
+    if setup:
+        setup(a)
+        setup(b)
+    a.step(n1)
+    path = tmp_path / "ckpt.bin"
+    a.save(path)
+    la, _ = a.step(n2, trace_logpost=True)
+    b.load(path)
+    lb, _ = b.step(n2, trace_logpost=True)
+    sa, sb = a.state(), b.state()
+    torch.cuda.synchronize()
+    assert torch.equal(la, lb)
+    for x, y in zip(sa, sb):
+        assert torch.equal(x, y)
+    return a, b, path
+
+
+def test_checkpoint_resumes_bit_for_bit(cuda_lib, tmp_path):
+    api = cuda_lib
+    K, C = 4, 16
+    make = lambda: _make_sampler(api, K, C, 11, T=3000, precision="tf32", recheck=1)[0]  # noqa: E731
+    a, b, path = _run_pair(api, make, 5, 7, tmp_path)
+    ra, rb = a.fp32_report(), b.fp32_report()
+    torch.cuda.synchronize()
+    assert torch.equal(ra[0], rb[0])
+    # a sampler of another shape, or a file that is not a checkpoint, is refused
+    other = _make_sampler(api, K, C + 1, 11, T=3000)[0]
+    with pytest.raises(api.HMMError) as e:
+        other.load(path)
+    assert e.value.code == api.HMM_EINVAL
+    bad = tmp_path / "junk.bin"
+    bad.write_bytes(b"not a checkpoint" * 10)
+    with pytest.raises(api.HMMError) as e:
+        a.load(bad)
+    assert e.value.code == api.HMM_EINVAL
+    with pytest.raises(api.HMMError):
+        a.load(tmp_path / "missing.bin")
+    a.close(); b.close(); other.close()
+
+
+def test_checkpoint_resumes_twalk_and_learned(cuda_lib, tmp_path):
+    api = cuda_lib
+    K, C = 4, 16
+
+    def make():
+        return _make_sampler(api, K, C, 12, T=2000)[0]
+
+    def twalk(s):
+        th = s.state()[0]
+        g = torch.Generator(device="cuda").manual_seed(5)
+        s.set_twalk((th + 0.01 * torch.randn(th.shape, device="cuda", generator=g)).contiguous())
+
+    a, b, _ = _run_pair(api, make, 4, 6, tmp_path, setup=twalk)
+    ta, tb = a.twalk_state(), b.twalk_state()
+    assert torch.equal(ta[0], tb[0]) and torch.equal(ta[1], tb[1])
+    a.close(); b.close()
+
+    D = api.theta_dim(K)
+    nets = []
+
+    def learned(s):
+        m = api.MLP(D, hidden=32, seed=len(nets))
+        nets.append(m)
+        X = s.state()[0].repeat(8, 1).contiguous()
+        Y = (X + 0.01 * torch.randn_like(X)).contiguous()
+        m.fit_scaling(X, Y, 0.5)
+        if len(nets) == 1:
+            m.train(X, Y, 20, batch=64, lr=1e-3, seed=3)
+        m.set_lambda(0.5, 0.3)
+        s.set_proposal(m)
+
+    # B's network starts different (other seed, untrained): the load overwrites it
+    a, b, _ = _run_pair(api, make, 3, 5, tmp_path, setup=learned)
+    pa, pb = nets[0].get_params(), nets[1].get_params()
+    torch.cuda.synchronize()
+    assert torch.equal(pa, pb)
+    a.close(); b.close()
