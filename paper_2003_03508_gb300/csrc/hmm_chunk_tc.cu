@@ -28,6 +28,8 @@
 // Every wait is bounded: a wait that runs out sets the context's ETIMEOUT
 // status bit and an abort flag; all warps then drain (in-flight copies and
 // MMAs) and return, and the TMEM is freed.
+#include <type_traits>
+
 #include "hmm_tc_common.cuh"
 
 namespace hmm {
@@ -131,6 +133,13 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
         if (lane == 0) {
             const uint32_t idesc = instr_desc<PREC>(KP);
             const uint32_t p_base = smem_u32(smem + C::OFF_P);
+            // B descriptors of every MMA of a group-step (P's images never move)
+            uint64_t bd[C::NIMG * C::NKS];
+#pragma unroll
+            for (int img = 0; img < C::NIMG; ++img)
+#pragma unroll
+                for (int ks = 0; ks < C::NKS; ++ks)
+                    bd[img * C::NKS + ks] = smem_desc(p_base + img * (KP * KP * C::ESZ) + ks * 256, 128, C::SBO);
             uint32_t empty_par = 0, pload_par = 0;
             bool ok = true, issued = false;
             for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
@@ -147,15 +156,8 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
                         tc_fence_after();
                         const uint32_t d_tmem = tmem_base + (uint32_t)(g * KP);
                         const uint32_t a_tmem = tmem_base + (uint32_t)(C::A_COL0 + g * C::KA);
-#pragma unroll
-                        for (int img = 0; img < C::NIMG; ++img) {
-#pragma unroll
-                            for (int ks = 0; ks < C::NKS; ++ks) {
-                                // one MMA consumes 32 bytes of K: 8 TMEM columns of A
-                                const uint64_t bd = smem_desc(p_base + img * (KP * KP * C::ESZ) + ks * 256, 128, C::SBO);
-                                mma_ts<PREC>(d_tmem, a_tmem + ks * 8, bd, idesc, (img | ks) != 0);
-                            }
-                        }
+                        // one MMA consumes 32 bytes of K: 8 TMEM columns of A
+                        mma_group<PREC, C::NIMG, C::NKS>(d_tmem, a_tmem, bd, idesc);
                         mma_commit(&full[g]);
                         issued = true;
                     }
@@ -264,10 +266,227 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
                 cp_async_commit();
             }
 
-            const bool fast = (renorm == FAST_R) && (steps % FAST_R == 0);
+            // The fast path covers the default renormalisation interval with
+            // TF32 operands (BF16 packs two operands per TMEM column, which the
+            // 16x256b fragment below does not match).
+            const bool fast = (renorm == FAST_R) && (PREC != HMM_PREC_BF16 || steps % FAST_R == 0);
             bool bad = false;
+            if constexpr (PREC != HMM_PREC_BF16) {
             if (fast) {
-                // ---- fast path: four steps per trip, renormalisation on the fourth ----
+                // ---- fast path: trips of four steps, renormalisation on the fourth ----
+                // TMEM is read and written in the 16x256b fragment: this thread
+                // holds rows 8*rho + g8 (rho = 0..3) of its warp's 32 lanes,
+                // columns 8m + 2*qd + {0, 1} (m < NB), so it needs only 2*NB of
+                // the KP emission factors of a step, read as float4s from a
+                // permuted copy in shared memory; the four threads of a quad
+                // share a row and combine their row maxima by two shuffles.
+                constexpr int NB = KP / 8;
+                constexpr int NV = 4 * NB;
+                const int g8 = lane >> 2, qd = lane & 3;
+                int lenw[C::GPW][C::CPW];
+#pragma unroll
+                for (int u = 0; u < C::GPW; ++u)
+#pragma unroll
+                    for (int cw = 0; cw < C::CPW; ++cw) lenw[u][cw] = __shfl_sync(0xffffffffu, len[u], cw * KP);
+                int ex[C::GPW][4];
+                int esum[C::GPW];
+#pragma unroll
+                for (int u = 0; u < C::GPW; ++u) {
+                    esum[u] = 0;
+#pragma unroll
+                    for (int rho = 0; rho < 4; ++rho) ex[u][rho] = 0;
+                }
+                // this lane's emission factor goes to position pd of its chunk's factors
+                const int pd = half * KP + (2 * NB) * ((jl >> 1) & 3) + 2 * (jl >> 3) + (jl & 1);
+                // TF32 (one image of P): the tensor core truncates the running
+                // product to its top 19 bits; the mean relative loss per step
+                // is restored by scaling every step's emissions by 1/(1 - c)
+                // (c below), except at a chunk's first step, whose operand (the
+                // identity) is exact
+                constexpr bool TRUNC = (PREC == HMM_PREC_TF32);
+                const float comp = TRUNC ? TF32_TRUNC_COMP_LOG2 : 0.0f;
+
+                auto step = [&](int t, int rr, auto SPEC) {
+                    constexpr bool spec = decltype(SPEC)::value;
+                    const int w = t & (C::WIN - 1);
+                    const int bsel = (t / C::WIN) & 1;
+                    const float cadd = (t == 0) ? 0.0f : comp;
+                    int Et[C::GPW];
+#pragma unroll
+                    for (int u = 0; u < C::GPW; ++u) {
+                        const float2 o = win_ptr(u, bsel)[w];
+                        const float dx = o.x - mux, dy = o.y - muy;
+                        float l = fmaf(qa * dx, dx, fmaf(qb * dx, dy, fmaf(qc * dy, dy, ctr)));
+                        l = (isnan(o.x) ? cno : l) + cadd;
+                        const float m = chunk_max<KP>(l, lane);
+                        float mf;
+                        const int e = round_to_int(m, mf);
+                        const bool ok = m >= -(float)EXP_LIMIT;
+                        Et[u] = ok ? e : 0;
+                        const float d = ex2_approx(l - mf);
+                        if (!ok && m != -INFINITY && t < len[u]) atomicOr(status, ST_ENUMERIC);
+                        sD[u * 32 + pd] = ok ? d : 0.0f;
+                        if (!spec || t < len[u]) esum[u] += Et[u];
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int u = 0; u < C::GPW; ++u) {
+                        const int g = team + E * u;
+                        if (!(glive >> u & 1u)) continue;
+                        const bool okw =
+                            __all_sync(0xffffffffu, mbar_wait(&full[g], (full_par >> g) & 1u, abort_flag, status));
+                        full_par ^= 1u << g;
+                        if (!okw) {
+                            bad = true;
+                            return;
+                        }
+                        tc_fence_after();
+                        float v[2][NV];
+                        tmem_ld_16x256b<NB>(tm_row + g * KP, v[0]);
+                        tmem_ld_16x256b<NB>(tm_row + (16u << 16) + g * KP, v[1]);
+                        tmem_wait_ld();
+                        // the emission factors this thread needs, per chunk of the warp
+                        float dv[C::CPW][2 * NB];
+#pragma unroll
+                        for (int cw = 0; cw < C::CPW; ++cw) {
+                            const float4 *src = reinterpret_cast<const float4 *>(sD + u * 32 + cw * KP + 2 * NB * qd);
+#pragma unroll
+                            for (int k = 0; k < NB / 2; ++k) {
+                                const float4 f = src[k];
+                                dv[cw][4 * k] = f.x;
+                                dv[cw][4 * k + 1] = f.y;
+                                dv[cw][4 * k + 2] = f.z;
+                                dv[cw][4 * k + 3] = f.w;
+                            }
+                        }
+                        // column scale (Step 2 fused), paired multiplies
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int cw = (KP == 32) ? 0 : h;
+#pragma unroll
+                            for (int mm = 0; mm < NB; ++mm) {
+                                const unsigned long long dd = pack2(dv[cw][2 * mm], dv[cw][2 * mm + 1]);
+#pragma unroll
+                                for (int hi = 0; hi < 2; ++hi) {
+                                    float &a0 = v[h][4 * mm + 2 * hi], &a1 = v[h][4 * mm + 2 * hi + 1];
+                                    unpack2(mul2(pack2(a0, a1), dd), a0, a1);
+                                }
+                            }
+                        }
+                        // per-row power-of-two renormalisation, and a chunk's final write-out
+                        bool rn[4], fin[4], live[4];
+#pragma unroll
+                        for (int rho = 0; rho < 4; ++rho) {
+                            const int cw = (KP == 32) ? 0 : (rho >> 1);
+                            fin[rho] = spec && (t + 1 == lenw[u][cw]);
+                            live[rho] = t < lenw[u][cw];
+                            rn[rho] = (rr == FAST_R - 1) || fin[rho];
+                        }
+                        const bool any_rn = (rr == FAST_R - 1) || (spec && (fin[0] || fin[1] || fin[2] || fin[3]));
+                        // prescale exponent sums of the warp's chunks (for rows written now)
+                        int es[C::CPW];
+#pragma unroll
+                        for (int cw = 0; cw < C::CPW; ++cw) es[cw] = spec ? __shfl_sync(0xffffffffu, esum[u], cw * KP) : 0;
+                        if (any_rn) {
+                            bool nonfinite = false;
+#pragma unroll
+                            for (int rho = 0; rho < 4; ++rho) {
+                                const int h = rho >> 1, hi = rho & 1;
+                                float mx = 0.0f;
+#pragma unroll
+                                for (int mm = 0; mm < NB; ++mm)
+                                    mx = max3f(mx, v[h][4 * mm + 2 * hi], v[h][4 * mm + 2 * hi + 1]);
+                                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+                                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+                                if (!rn[rho]) continue;
+                                uint32_t eb = __float_as_uint(mx) & 0x7f800000u;
+                                nonfinite |= live[rho] && eb == 0x7f800000u;
+                                eb = min(max(eb, 0x00800000u), 0x7e800000u);  // exponent in [-126, 126]
+                                const float sc = __uint_as_float(0x7f000000u - eb);
+                                ex[u][rho] += (int)(eb >> 23) - 127;
+                                const unsigned long long s2 = pack2(sc, sc);
+#pragma unroll
+                                for (int mm = 0; mm < NB; ++mm) {
+                                    float &a0 = v[h][4 * mm + 2 * hi], &a1 = v[h][4 * mm + 2 * hi + 1];
+                                    unpack2(mul2(pack2(a0, a1), s2), a0, a1);
+                                }
+                                if (spec && fin[rho]) {
+                                    // this row's chunk ends here: write the row and its exponent
+                                    const int cw = (KP == 32) ? 0 : h;
+                                    const int row = (KP == 32) ? 8 * rho + g8 : 8 * hi + g8;
+                                    const size_t jj = (size_t)q * n_chunks + (size_t)b * per_item + g * C::CPG +
+                                                      quad * C::CPW + cw;
+                                    float *dst = A0 + jj * KP * KP + (size_t)row * KP + 2 * qd;
+#pragma unroll
+                                    for (int mm = 0; mm < NB; ++mm)
+                                        *reinterpret_cast<float2 *>(dst + 8 * mm) =
+                                            make_float2(v[h][4 * mm + 2 * hi], v[h][4 * mm + 2 * hi + 1]);
+                                    if (qd == 0) e0[jj * KP + row] = (mx > 0.0f) ? ex[u][rho] + es[cw] : ZERO_ROW_EXP32;
+                                }
+                            }
+                            if (nonfinite) atomicOr(status, ST_ENUMERIC);
+                        }
+                        if (t + 1 < steps) {
+                            // next A operand (TF32: the raw FP32 bits, truncated by the
+                            // tensor core; TF32-split: rounded to nearest first)
+                            uint32_t wv[2][NV];
+#pragma unroll
+                            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                                for (int k = 0; k < NV; ++k)
+                                    wv[h][k] = TRUNC ? __float_as_uint(v[h][k]) : to_tf32_bits(v[h][k]);
+                            tmem_st_16x256b<NB>(tm_row + C::A_COL0 + g * C::KA, wv[0]);
+                            tmem_st_16x256b<NB>(tm_row + (16u << 16) + C::A_COL0 + g * C::KA, wv[1]);
+                            tmem_wait_st();
+                        }
+                        tc_fence_before();
+                        __syncwarp();
+                        if (t + 1 < steps && lane == 0) mbar_arrive(&empty[g]);
+                    }
+                };
+
+                for (int t0 = 0; t0 < steps && !bad; t0 += FAST_R) {
+                    const int bsel = (t0 / C::WIN) & 1;
+                    if ((t0 & (C::WIN - 1)) == 0) {
+                        if (t0 > 0) {
+#pragma unroll
+                            for (int u = 0; u < C::GPW; ++u) {
+#pragma unroll
+                                for (int vv = 0; vv < C::NWIN; ++vv) {
+                                    const int s = t0 + C::WIN + jl + KP * vv;
+                                    if (s < len[u]) cp_async8(smem_u32(win_ptr(u, bsel ^ 1) + jl + KP * vv), packed + pstart[u] + s);
+                                }
+                            }
+                            cp_async_commit();
+                        }
+                        cp_async_wait1();
+                        __syncwarp();
+                    }
+                    // a trip in which a chunk of this warp ends, or the item's last
+                    // trip, takes the per-row checks; every other trip runs without
+                    bool spec = t0 + FAST_R >= steps;
+#pragma unroll
+                    for (int u = 0; u < C::GPW; ++u)
+#pragma unroll
+                        for (int cw = 0; cw < C::CPW; ++cw)
+                            spec |= (unsigned)(lenw[u][cw] - 1 - t0) < (unsigned)FAST_R;
+                    if (!spec) {
+#pragma unroll
+                        for (int rr = 0; rr < FAST_R; ++rr) {
+                            step(t0 + rr, rr, std::integral_constant<bool, false>());
+                            if (bad) break;
+                        }
+                    } else {
+                        for (int rr = 0; rr < FAST_R && t0 + rr < steps; ++rr) {
+                            step(t0 + rr, rr, std::integral_constant<bool, true>());
+                            if (bad) break;
+                        }
+                    }
+                }
+            }
+            } else {
+            if (fast) {
+                // ---- BF16 fast path: four steps per trip, renormalisation on the fourth ----
                 for (int t0 = 0; t0 < steps && !bad; t0 += FAST_R) {
                     const int bsel = (t0 / C::WIN) & 1;
                     if ((t0 & (C::WIN - 1)) == 0) {
@@ -357,6 +576,7 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
                         if (bad) break;
                     }
                 }
+            }
             }
             int rcount = renorm;
             for (int t = 0; t < steps && !fast; ++t) {

@@ -16,6 +16,13 @@ constexpr int TC_M = 128;
 constexpr int NISS = 4;  // MMA issuer warps (warps 0..3)
 constexpr int FAST_R = 4;  // renormalisation interval of the unrolled fast path
 constexpr long long SPIN_LIMIT_CYCLES = 4000000000LL;  // about 2 s at 2 GHz
+// A TF32 operand read from FP32 bits keeps the top 10 mantissa bits: the
+// dropped part is a fraction U * 2^-10 / m of the value (U uniform in [0, 1),
+// m in [1, 2) the mantissa), whose mean over log-uniformly spread mantissas
+// is c = 2^-11 * E[1/m] = 2^-11 / (2 ln 2). Multiplying a step's emission
+// factors by 1 / (1 - c), i.e. adding -log2(1 - c) to their log2, restores
+// the mean loss of the truncated step.
+constexpr float TF32_TRUNC_COMP_LOG2 = 5.0823623e-4f;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -218,6 +225,62 @@ __device__ __forceinline__ void tmem_st_row(uint32_t taddr, const uint32_t *r) {
 __device__ __forceinline__ void tmem_wait_st() {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
+
+// ---- 16x256b access: 16 TMEM lanes x 8 32-bit columns per repetition ----
+// Thread t of the warp holds, for repetition m (columns 8m .. 8m+7 from the
+// address's column), registers 4m+0/1 = lane (t/4), columns 8m + 2(t%4) + 0/1
+// and registers 4m+2/3 = lane (t/4 + 8), the same columns. A row of 8 columns
+// is therefore spread over the four threads of a quad, and each thread needs
+// only 2 of every 8 column factors.
+template <int NB>
+__device__ __forceinline__ void tmem_ld_16x256b(uint32_t taddr, float *v) {
+    static_assert(NB == 2 || NB == 4, "16x256b repetitions");
+    uint32_t r[4 * NB];
+    if constexpr (NB == 4) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.16x256b.x4.b32 "
+            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+              "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+    } else {
+        asm volatile("tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                       "=r"(r[7])
+                     : "r"(taddr));
+    }
+#pragma unroll
+    for (int i = 0; i < 4 * NB; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int NB>
+__device__ __forceinline__ void tmem_st_16x256b(uint32_t taddr, const uint32_t *r) {
+    static_assert(NB == 2 || NB == 4, "16x256b repetitions");
+    if constexpr (NB == 4) {
+        asm volatile(
+            "tcgen05.st.sync.aligned.16x256b.x4.b32 [%0], "
+            "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+            "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+            "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+            : "memory");
+    } else {
+        asm volatile("tcgen05.st.sync.aligned.16x256b.x2.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+                     "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                     : "memory");
+    }
+}
+
+// All MMAs of one group-step (NIMG images of P x NKS slices of K), the first
+// overwriting D, the rest accumulating; B descriptors precomputed.
+template <int PREC, int NIMG, int NKS>
+__device__ __forceinline__ void mma_group(uint32_t d_tmem, uint32_t a_tmem, const uint64_t *bd, uint32_t idesc) {
+#pragma unroll
+    for (int img = 0; img < NIMG; ++img)
+#pragma unroll
+        for (int ks = 0; ks < NKS; ++ks) mma_ts<PREC>(d_tmem, a_tmem + ks * 8, bd[img * NKS + ks], idesc, (img | ks) != 0);
+}
+
 
 // FP32 -> TF32 operand, round to nearest with ties away from zero: add half a
 // TF32 unit in the last place to the bit pattern (integer pipe; overflow

@@ -234,9 +234,9 @@ def test_fp32_recheck_reports_and_leaves_the_chains_alone(cuda_lib):
     The stored log likelihoods stay the TF32 evaluations of the states; the
     report holds FP32 values that match the FP64 oracle."""
     api = cuda_lib
-    K, C, n = 16, 16, 6
-    a, th0, step, obs, pr = _make_sampler(api, K, C, 5, T=20000, step_scale=0.01, precision="tf32", recheck=1)
-    b, *_ = _make_sampler(api, K, C, 5, T=20000, step_scale=0.01, precision="tf32", recheck=0)
+    K, C, n = 6, 24, 20
+    a, th0, step, obs, pr = _make_sampler(api, K, C, 21, T=5000, step_scale=0.02, precision="tf32", recheck=1)
+    b, *_ = _make_sampler(api, K, C, 21, T=5000, step_scale=0.02, precision="tf32", recheck=0)
     assert torch.isnan(a.fp32_report()[0]).all()  # nothing rechecked yet
     la = torch.cat([a.step(1, trace_logpost=True)[0] for _ in range(n)])
     lb, _ = b.step(n, trace_logpost=True)
@@ -279,9 +279,9 @@ def test_tf32_decisions_use_tf32_values_on_both_sides(cuda_lib):
     gen = synth.random_params(K, rng)
     obs = synth.sample_observations(gen, 4000, rng)
     th0 = _near_truth(K, C, gen, rng, scale=0.02)
-    step = np.full(D, 0.02, np.float32)
+    step = np.full(D, 0.01, np.float32)
     o0 = K * (K - 1) + (K - 1) + K
-    step[o0:o0 + 2 * K] = 1.0
+    step[o0:o0 + 2 * K] = 0.5
     pr = api.make_prior(K, alpha_P=0.5)
     xy, fl = torch.from_numpy(obs.xy).cuda(), torch.from_numpy(obs.tremor).cuda()
     opts = api.make_opts(precision="tf32", chunk_len=256, recheck_fp32=1)
