@@ -178,6 +178,38 @@ int hmm_expected_stats(hmm_ctx *ctx, const hmm_params *params, const hmm_obs *ob
                        double *stats, double *loglik, void *stream);
 
 /*
+ * Gradient of log L with respect to every parameter of one parameter set,
+ * for gradient-based fitting and samplers, by the Fisher identity: the
+ * posterior expectation of the gradient of the complete-data log likelihood
+ * of Section 2 (hidden path, transitions P, emissions of Eq.
+ * "emission-matrix"), formed in FP64 on the device from the statistics of
+ * hmm_expected_stats (same options, same chunked forward-backward pass).
+ * grad (device, K*K + 7*K doubles) receives, in the order of hmm_params,
+ *   d/dpi [K], d/dP [K*K] (row-major), d/dp_tremor [K], d/dmu [K*2],
+ *   d/dcov [K*3] (sxx, sxy, syy; sxy enters both off-diagonal entries),
+ * with pi and P differentiated as free entries (no simplex constraint) and
+ * opts->init_mode choosing where pi enters; *loglik (device double) receives
+ * log L. Terms whose expected count is zero contribute zero. T >= 2.
+ */
+int hmm_loglik_grad(hmm_ctx *ctx, const hmm_params *params, const hmm_obs *obs, const hmm_opts *opts,
+                    double *grad, double *loglik, void *stream);
+
+/*
+ * One EM (Baum-Welch) iteration: the E-step statistics of hmm_expected_stats
+ * and the M-step that maximises the expected complete-data log likelihood,
+ *   P_ij = N_ij / sum_j N_ij, pi = G0 / sum G0, p_k = Gr_k / Gs_k,
+ *   mu_k = (Sx_k, Sy_k) / Gr_k, Sigma_k = (second moments) / Gr_k - mu_k mu_k^T,
+ * written as float32 parameters to pi_out [K], P_out [K*K], p_out [K],
+ * mu_out [K*2], cov_out [K*3] (device; may not alias the inputs); a row of P
+ * or a state whose expected count is zero keeps its input value. *loglik
+ * (device double) receives log L of the INPUT parameters; the likelihood of
+ * the output is never lower (EM's monotonicity), up to the arithmetic's
+ * rounding. Emit-first convention only (HMM_EUNSUPPORTED otherwise). T >= 2.
+ */
+int hmm_em_step(hmm_ctx *ctx, const hmm_params *params, const hmm_obs *obs, const hmm_opts *opts, float *pi_out,
+                float *P_out, float *p_out, float *mu_out, float *cov_out, double *loglik, void *stream);
+
+/*
  * log L for one parameter set and one sequence (Eq. "likelihood func",
  * computed as Section "The likelihood algorithm" restructures it).
  * out_dev: device pointer to one double.

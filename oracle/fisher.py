@@ -1,6 +1,7 @@
-"""Gradient of log L and the EM update from the hidden chain's expected
-sufficient statistics (host-side algebra on K-sized arrays; the statistics
-themselves come from the library's kernels, `Context.hmm_expected_stats`).
+"""Fisher-identity gradient of log L and the EM (Baum-Welch) update from the
+hidden chain's expected sufficient statistics -- the oracle's statement of
+that algebra (test infrastructure only), applied to statistics from
+``oracle.expected_stats``.
 
 Fisher identity: the gradient of the log likelihood equals the posterior
 expectation of the gradient of the complete-data log likelihood,
@@ -15,9 +16,10 @@ and for pi (emit-first) d/dpi_k = G0_k / pi_k. P and pi are treated as free
 entries (no simplex constraint); the covariance is parameterised by
 (sxx, sxy, syy), sxy entering both off-diagonal entries.
 
-The EM (Baum-Welch) update maximises the expected complete-data log
-likelihood: P_ij = N_ij / sum_j N_ij, pi = G0, p_k = Gr_k / Gs_k, mu_k = S_k /
-Gr_k, Sigma_k = Q_k / Gr_k.
+The EM update maximises the expected complete-data log likelihood:
+P_ij = N_ij / sum_j N_ij, pi = G0, p_k = Gr_k / Gs_k, mu_k = S_k / Gr_k,
+Sigma_k = Q_k / Gr_k. Pinned in tests/test_oracle_stats.py (central finite
+differences of the likelihood oracle, EM monotonicity).
 """
 from __future__ import annotations
 
@@ -27,7 +29,7 @@ import numpy as np
 def loglik_gradient(pi, P, p, mu, cov, st, init_mode: int = 0):
     """d log L / d (pi, P, p_tremor, mu, cov) as float64 arrays of the
     parameters' shapes, from the statistics dict `st` that
-    Context.hmm_expected_stats returns (N [K, K]; G0, Gs, Gr, Sx, Sy, Sxx,
+    oracle.expected_stats returns (N [K, K]; G0, Gs, Gr, Sx, Sy, Sxx,
     Sxy, Syy [K])."""
     pi, P, p, mu, cov = (np.asarray(a, dtype=np.float64) for a in (pi, P, p, mu, cov))
     K = pi.shape[0]

