@@ -7,9 +7,15 @@ one call of hmm_loglik_batched, i.e. every stage of the likelihood path
 (parameter constants, observation packing, chunk products, product tree,
 FP64 combine). Inputs are resident in HBM when the timed region starts; the
 L2 is flushed (a 256 MiB write) between timed steps, outside the events.
+Before the warm-up the chunk length is tuned for this shape by the library's
+autotuner (hmm_autotune_batched, untimed); the timed calls use the stored
+length (chunk_len = 0).
 
 Also reported on the same line:
-  plain_gpu     the same metric with the FP32-SIMT chunk products;
+  plain_gpu     the same metric with the FP32-SIMT chunk products (same
+                workload, all proposals);
+  tf32_split    the same metric with TF32 chunk products whose P is carried
+                as hi + lo (two MMAs): FP32-like accuracy on the tensor cores;
   e2e           the same metric through hmm_loglik_batched_host (pinned host
                 buffers, host->device inputs and device->host results inside
                 the timed region);
@@ -61,8 +67,9 @@ def parse():
     ap.add_argument("--T", type=int, default=1 << 20)
     ap.add_argument("--n-prop", type=int, default=256)
     ap.add_argument("--chunk-len", type=int, default=0)
-    ap.add_argument("--autotune", action="store_true",
-                    help="measure the candidate chunk lengths first (hmm_autotune_batched) and run at the fastest")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip measuring the candidate chunk lengths (hmm_autotune_batched) before the timed steps")
+    ap.add_argument("--no-split", action="store_true", help="skip the TF32-split (P as hi + lo) sub-line")
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -350,7 +357,7 @@ def main():
         ctx.hmm_loglik_batched(*dev, offs, xy, fl, opts=opts, out=out)
 
     tuned = None
-    if args.autotune and args.chunk_len == 0:
+    if not args.no_autotune and args.chunk_len == 0:
         # untimed: the tuner stores the fastest chunk length for this shape and
         # the automatic choice (chunk_len = 0) in the timed steps uses it
         _, tL, tms = ctx.hmm_autotune_batched(*dev, offs, xy, fl, opts=opts, reps=3, out=out)
@@ -426,27 +433,38 @@ def main():
     if tuned:
         result["autotune"] = tuned
 
-    # plain GPU (FP32-SIMT chunk products) on the same workload, fewer proposals
+    def timed_variant(precision, reps=2):
+        """The same workload and proposals with other chunk products (untimed
+        warm-up call, then `reps` event-timed calls, L2 flushed before each)."""
+        vo = api.make_opts(precision=precision)
+        vout = torch.empty(args.n_prop, dtype=torch.float64, device="cuda")
+        ctx.hmm_loglik_batched(*dev, offs, xy, fl, opts=vo, out=vout)
+        torch.cuda.synchronize()
+        ms = 0.0
+        for i in range(reps):
+            flush.fill_(i & 0xff)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.hmm_loglik_batched(*dev, offs, xy, fl, opts=vo, out=vout)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        ms = max_over_ranks(ms, world, "cuda") / reps
+        return {"value": job_rate(args.n_prop, world, ms), "unit": UNIT, "precision": precision,
+                "n_prop": args.n_prop, "ms_per_step": ms, "chunk_len": ctx.last_chunk_len}, vout
+
+    # plain GPU (FP32-SIMT chunk products) on the same workload and proposals
+    variant_out = {}
     if not args.no_plain and args.precision != "fp32":
-        n_plain = min(args.n_prop, 32)
-        sub = tuple(t[:n_plain].contiguous() for t in dev)
-        po = api.make_opts(precision="fp32")
-        pout = torch.empty(n_plain, dtype=torch.float64, device="cuda")
-        ctx.hmm_loglik_batched(*sub, offs, xy, fl, opts=po, out=pout)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(2):
-            ctx.hmm_loglik_batched(*sub, offs, xy, fl, opts=po, out=pout)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        pms = e0.elapsed_time(e1) / 2
-        result["plain_gpu"] = {"value": world * n_plain / (pms / 1e3), "unit": UNIT,
-                               "precision": "fp32_simt", "n_prop": n_plain, "ms_per_step": pms}
-        d = (out[:n_plain] - pout).abs().max().item()
-        result["plain_gpu"]["max_abs_diff_vs_tc"] = d
-        plain_out = pout.cpu().numpy()
+        result["plain_gpu"], pout = timed_variant("fp32")
+        result["plain_gpu"]["precision"] = "fp32_simt"
+        result["plain_gpu"]["max_abs_diff_vs_tc"] = float((out - pout).abs().max().item())
+        variant_out["plain_gpu"] = pout.cpu().numpy()
+    # TF32 with P carried as hi + lo (two MMAs): the tensor-core figure at FP32-like accuracy
+    if not args.no_split and args.precision == "tf32":
+        result["tf32_split"], sout = timed_variant("tf32_split")
+        variant_out["tf32_split"] = sout.cpu().numpy()
 
     # run-length shortcut on the sparse-tremor workload of the same size
     if not args.no_runlen:
@@ -505,10 +523,10 @@ def main():
         result["error_vs_oracle"] = {"dtype": args.precision, "proposals": int(n_sample),
                                      "max_rel": float(rel.max()), "max_abs": float(np.abs(got - ref).max()),
                                      "log_lik_mean": float(ref.mean())}
-        if "plain_gpu" in result:
-            pg = plain_out[:min(n_sample, plain_out.shape[0])]
-            relp = np.abs(pg - ref[:pg.shape[0]]) / np.abs(ref[:pg.shape[0]])
-            result["plain_gpu"]["max_rel_vs_oracle"] = float(relp.max())
+        for name, vals in variant_out.items():
+            relv = np.abs(vals[:n_sample] - ref) / np.abs(ref)
+            result[name]["max_rel_vs_oracle"] = float(relv.max())
+            result[name]["max_abs_vs_oracle"] = float(np.abs(vals[:n_sample] - ref).max())
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:
