@@ -89,11 +89,13 @@ def _ess_summary(lp, summ, K):
 
 def rw_vs_learned(K=16, T=16384, chains=512, seed=0, burn=3000, history=200, lag=20, hidden=256,
                   train_steps=2000, batch=512, lr=2e-3, n_measure=1000, alpha_P=0.5,
-                  target_accept=0.25, opts=None, cross=True):
+                  target_accept=0.25, opts=None, cross=True, pilot_iters=100,
+                  pcn_rhos=(0.9, 0.97, 0.99, 0.995, 0.998), rw_lams=(0.25, 0.12, 0.06)):
     """Tune and burn in the random walk, train the learned proposal on its
     history (cross=True: pairs of different chains at the same iteration,
     else pairs `lag` iterations apart in one chain), pick its step factor and
-    drift factor by the expected squared jump distance of short pilots, then
+    drift factor by the expected squared jump distance of short pilots (the
+    autoregressive pairs of learned.pcn_pairs and drift-free steps), then
     run both samplers for n_measure iterations from the same states and
     report effective samples per second of the log posterior and of the
     label-invariant summaries (Geyer initial monotone sequence estimator,
@@ -132,8 +134,8 @@ def rw_vs_learned(K=16, T=16384, chains=512, seed=0, burn=3000, history=200, lag
     ls = make(th_now, step, seed + 3)
     mlp, info = learned.fit_learned_proposal(ls, hist, lag=lag, hidden=hidden, train_steps=train_steps,
                                              batch=batch, lr=lr, seed=seed + 4, target_accept=target_accept,
-                                             lams=(1.0, 0.5, 0.25, 0.12, 0.06), gammas=(1.0, 0.5, 0.2, 0.0),
-                                             select="esjd", pilot_iters=100, cross=cross)
+                                             pairs=learned.pcn_pairs(pcn_rhos) + [(lam, 0.0) for lam in rw_lams],
+                                             select="esjd", pilot_iters=pilot_iters, cross=cross)
     fit_s = time.perf_counter() - t0
     del hist
 

@@ -274,14 +274,15 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
             if constexpr (PREC != HMM_PREC_BF16) {
             if (fast) {
                 // ---- fast path: trips of four steps, renormalisation on the fourth ----
-                // TMEM is read and written in the 16x256b fragment: this thread
-                // holds rows 8*rho + g8 (rho = 0..3) of its warp's 32 lanes,
-                // columns 8m + 2*qd + {0, 1} (m < NB), so it needs only 2*NB of
-                // the KP emission factors of a step, read as float4s from a
+                // TMEM is read and written in the 16x256b fragment, kept as
+                // 64-bit pairs of adjacent columns: this thread holds rows
+                // 8*rho + g8 (rho = 0..3) of its warp's 32 lanes, columns
+                // 8m + 2*qd + {0, 1} (m < NB), so it needs only 2*NB of the KP
+                // emission factors of a step, read as 16-byte words from a
                 // permuted copy in shared memory; the four threads of a quad
                 // share a row and combine their row maxima by two shuffles.
                 constexpr int NB = KP / 8;
-                constexpr int NV = 4 * NB;
+                constexpr int NP = 4 * NB;  // pairs per thread (both halves)
                 const int g8 = lane >> 2, qd = lane & 3;
                 int lenw[C::GPW][C::CPW];
 #pragma unroll
@@ -290,9 +291,11 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
                     for (int cw = 0; cw < C::CPW; ++cw) lenw[u][cw] = __shfl_sync(0xffffffffu, len[u], cw * KP);
                 int ex[C::GPW][4];
                 int esum[C::GPW];
+                uint32_t gbit[C::GPW];
 #pragma unroll
                 for (int u = 0; u < C::GPW; ++u) {
                     esum[u] = 0;
+                    gbit[u] = 1u << (team + E * u);
 #pragma unroll
                     for (int rho = 0; rho < 4; ++rho) ex[u][rho] = 0;
                 }
@@ -301,32 +304,37 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
                 // TF32 (one image of P): the tensor core truncates the running
                 // product to its top 19 bits; the mean relative loss per step
                 // is restored by scaling every step's emissions by 1/(1 - c)
-                // (c below), except at a chunk's first step, whose operand (the
-                // identity) is exact
+                // (c in hmm_tc_common.cuh). A chunk's first step multiplies the
+                // exact identity, so its compensation is taken back when the
+                // chunk is written.
                 constexpr bool TRUNC = (PREC == HMM_PREC_TF32);
-                const float comp = TRUNC ? TF32_TRUNC_COMP_LOG2 : 0.0f;
+                const float ctr_s = ctr + (TRUNC ? TF32_TRUNC_COMP_LOG2 : 0.0f);
+                const float cno_s = cno + (TRUNC ? TF32_TRUNC_COMP_LOG2 : 0.0f);
+                const float uncomp = TRUNC ? ex2_approx(-TF32_TRUNC_COMP_LOG2) : 1.0f;
+                // smallest finite best-state log2 emission of the live steps
+                // (below -EXP_LIMIT is out of range; checked once per item)
+                float mlow = 0.0f;
+                const float2 *wbase[C::GPW];
 
                 auto step = [&](int t, int rr, auto SPEC) {
                     constexpr bool spec = decltype(SPEC)::value;
                     const int w = t & (C::WIN - 1);
-                    const int bsel = (t / C::WIN) & 1;
-                    const float cadd = (t == 0) ? 0.0f : comp;
                     int Et[C::GPW];
 #pragma unroll
                     for (int u = 0; u < C::GPW; ++u) {
-                        const float2 o = win_ptr(u, bsel)[w];
+                        // Step 1 fused: log2 emission of this lane's state (Eq.
+                        // "emission-matrix"), the chunk's best state, the
+                        // power-of-two prescale and the factor D_t
+                        const float2 o = wbase[u][w];
                         const float dx = o.x - mux, dy = o.y - muy;
-                        float l = fmaf(qa * dx, dx, fmaf(qb * dx, dy, fmaf(qc * dy, dy, ctr)));
-                        l = (isnan(o.x) ? cno : l) + cadd;
+                        const float l2 = fmaf(fmaf(qa, dx, qb * dy), dx, fmaf(qc * dy, dy, ctr_s));
+                        const float l = isnan(o.x) ? cno_s : l2;
                         const float m = chunk_max<KP>(l, lane);
+                        if (t < len[u] && m > -INFINITY) mlow = fminf(mlow, m);
                         float mf;
-                        const int e = round_to_int(m, mf);
-                        const bool ok = m >= -(float)EXP_LIMIT;
-                        Et[u] = ok ? e : 0;
-                        const float d = ex2_approx(l - mf);
-                        if (!ok && m != -INFINITY && t < len[u]) atomicOr(status, ST_ENUMERIC);
-                        sD[u * 32 + pd] = ok ? d : 0.0f;
-                        if (!spec || t < len[u]) esum[u] += Et[u];
+                        Et[u] = round_to_int(fmaxf(m, -(float)EXP_LIMIT), mf);
+                        sD[u * 32 + pd] = ex2_approx(l - mf);
+                        esum[u] += Et[u];
                     }
                     __syncwarp();
 #pragma unroll
@@ -334,93 +342,73 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
                         const int g = team + E * u;
                         if (!(glive >> u & 1u)) continue;
                         const bool okw =
-                            __all_sync(0xffffffffu, mbar_wait(&full[g], (full_par >> g) & 1u, abort_flag, status));
-                        full_par ^= 1u << g;
+                            __all_sync(0xffffffffu, mbar_wait(&full[g], (full_par & gbit[u]) ? 1u : 0u, abort_flag, status));
+                        full_par ^= gbit[u];
                         if (!okw) {
                             bad = true;
                             return;
                         }
                         tc_fence_after();
-                        float v[2][NV];
-                        tmem_ld_16x256b<NB>(tm_row + g * KP, v[0]);
-                        tmem_ld_16x256b<NB>(tm_row + (16u << 16) + g * KP, v[1]);
-                        tmem_wait_ld();
-                        // the emission factors this thread needs, per chunk of the warp
-                        float dv[C::CPW][2 * NB];
-#pragma unroll
-                        for (int cw = 0; cw < C::CPW; ++cw) {
-                            const float4 *src = reinterpret_cast<const float4 *>(sD + u * 32 + cw * KP + 2 * NB * qd);
-#pragma unroll
-                            for (int k = 0; k < NB / 2; ++k) {
-                                const float4 f = src[k];
-                                dv[cw][4 * k] = f.x;
-                                dv[cw][4 * k + 1] = f.y;
-                                dv[cw][4 * k + 2] = f.z;
-                                dv[cw][4 * k + 3] = f.w;
-                            }
-                        }
-                        // column scale (Step 2 fused), paired multiplies
+                        unsigned long long pr[NP];
+                        tmem_ld_pairs<NB>(tm_row + g * KP, tm_row + (16u << 16) + g * KP, pr);
+                        // Step 2 fused: column scale by D_t, paired multiplies
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             const int cw = (KP == 32) ? 0 : h;
+                            const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(sD + u * 32 + cw * KP + 2 * NB * qd);
 #pragma unroll
-                            for (int mm = 0; mm < NB; ++mm) {
-                                const unsigned long long dd = pack2(dv[cw][2 * mm], dv[cw][2 * mm + 1]);
+                            for (int k = 0; k < NB / 2; ++k) {
+                                const ulonglong2 dd = src[k];
 #pragma unroll
-                                for (int hi = 0; hi < 2; ++hi) {
-                                    float &a0 = v[h][4 * mm + 2 * hi], &a1 = v[h][4 * mm + 2 * hi + 1];
-                                    unpack2(mul2(pack2(a0, a1), dd), a0, a1);
+                                for (int j = 0; j < 2; ++j) {
+                                    pr[h * 2 * NB + 4 * k + j] = mul2(pr[h * 2 * NB + 4 * k + j], dd.x);
+                                    pr[h * 2 * NB + 4 * k + 2 + j] = mul2(pr[h * 2 * NB + 4 * k + 2 + j], dd.y);
                                 }
                             }
                         }
                         // per-row power-of-two renormalisation, and a chunk's final write-out
-                        bool rn[4], fin[4], live[4];
+                        bool fin[4];
 #pragma unroll
-                        for (int rho = 0; rho < 4; ++rho) {
-                            const int cw = (KP == 32) ? 0 : (rho >> 1);
-                            fin[rho] = spec && (t + 1 == lenw[u][cw]);
-                            live[rho] = t < lenw[u][cw];
-                            rn[rho] = (rr == FAST_R - 1) || fin[rho];
-                        }
+                        for (int rho = 0; rho < 4; ++rho) fin[rho] = spec && (t + 1 == lenw[u][(KP == 32) ? 0 : (rho >> 1)]);
                         const bool any_rn = (rr == FAST_R - 1) || (spec && (fin[0] || fin[1] || fin[2] || fin[3]));
-                        // prescale exponent sums of the warp's chunks (for rows written now)
-                        int es[C::CPW];
-#pragma unroll
-                        for (int cw = 0; cw < C::CPW; ++cw) es[cw] = spec ? __shfl_sync(0xffffffffu, esum[u], cw * KP) : 0;
                         if (any_rn) {
+                            int es[C::CPW];
+#pragma unroll
+                            for (int cw = 0; cw < C::CPW; ++cw) es[cw] = spec ? __shfl_sync(0xffffffffu, esum[u], cw * KP) : 0;
                             bool nonfinite = false;
 #pragma unroll
                             for (int rho = 0; rho < 4; ++rho) {
-                                const int h = rho >> 1, hi = rho & 1;
+                                const int h = rho >> 1, j = rho & 1;
+                                const int cw = (KP == 32) ? 0 : h;
                                 float mx = 0.0f;
 #pragma unroll
-                                for (int mm = 0; mm < NB; ++mm)
-                                    mx = max3f(mx, v[h][4 * mm + 2 * hi], v[h][4 * mm + 2 * hi + 1]);
+                                for (int mm = 0; mm < NB; ++mm) {
+                                    float a0, a1;
+                                    unpack2(pr[h * 2 * NB + 2 * mm + j], a0, a1);
+                                    mx = max3f(mx, a0, a1);
+                                }
                                 mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
                                 mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-                                if (!rn[rho]) continue;
+                                if (!((rr == FAST_R - 1) || fin[rho])) continue;
                                 uint32_t eb = __float_as_uint(mx) & 0x7f800000u;
-                                nonfinite |= live[rho] && eb == 0x7f800000u;
+                                nonfinite |= (t < lenw[u][cw]) && eb == 0x7f800000u;
                                 eb = min(max(eb, 0x00800000u), 0x7e800000u);  // exponent in [-126, 126]
                                 const float sc = __uint_as_float(0x7f000000u - eb);
                                 ex[u][rho] += (int)(eb >> 23) - 127;
                                 const unsigned long long s2 = pack2(sc, sc);
 #pragma unroll
-                                for (int mm = 0; mm < NB; ++mm) {
-                                    float &a0 = v[h][4 * mm + 2 * hi], &a1 = v[h][4 * mm + 2 * hi + 1];
-                                    unpack2(mul2(pack2(a0, a1), s2), a0, a1);
-                                }
+                                for (int mm = 0; mm < NB; ++mm)
+                                    pr[h * 2 * NB + 2 * mm + j] = mul2(pr[h * 2 * NB + 2 * mm + j], s2);
                                 if (spec && fin[rho]) {
                                     // this row's chunk ends here: write the row and its exponent
-                                    const int cw = (KP == 32) ? 0 : h;
-                                    const int row = (KP == 32) ? 8 * rho + g8 : 8 * hi + g8;
+                                    const int row = (KP == 32) ? 8 * rho + g8 : 8 * j + g8;
                                     const size_t jj = (size_t)q * n_chunks + (size_t)b * per_item + g * C::CPG +
                                                       quad * C::CPW + cw;
-                                    float *dst = A0 + jj * KP * KP + (size_t)row * KP + 2 * qd;
+                                    unsigned long long *dst =
+                                        reinterpret_cast<unsigned long long *>(A0 + jj * KP * KP + (size_t)row * KP + 2 * qd);
+                                    const unsigned long long un = pack2(uncomp, uncomp);
 #pragma unroll
-                                    for (int mm = 0; mm < NB; ++mm)
-                                        *reinterpret_cast<float2 *>(dst + 8 * mm) =
-                                            make_float2(v[h][4 * mm + 2 * hi], v[h][4 * mm + 2 * hi + 1]);
+                                    for (int mm = 0; mm < NB; ++mm) dst[4 * mm] = mul2(pr[h * 2 * NB + 2 * mm + j], un);
                                     if (qd == 0) e0[jj * KP + row] = (mx > 0.0f) ? ex[u][rho] + es[cw] : ZERO_ROW_EXP32;
                                 }
                             }
@@ -428,15 +416,14 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
                         }
                         if (t + 1 < steps) {
                             // next A operand (TF32: the raw FP32 bits, truncated by the
-                            // tensor core; TF32-split: rounded to nearest first)
-                            uint32_t wv[2][NV];
+                            // tensor core; TF32-split: rounded to nearest first, both
+                            // halves of a pair in one add: values are non-negative, so
+                            // the low half never carries)
+                            if constexpr (!TRUNC) {
 #pragma unroll
-                            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                                for (int k = 0; k < NV; ++k)
-                                    wv[h][k] = TRUNC ? __float_as_uint(v[h][k]) : to_tf32_bits(v[h][k]);
-                            tmem_st_16x256b<NB>(tm_row + C::A_COL0 + g * C::KA, wv[0]);
-                            tmem_st_16x256b<NB>(tm_row + (16u << 16) + C::A_COL0 + g * C::KA, wv[1]);
+                                for (int k = 0; k < NP; ++k) pr[k] += 0x0000100000001000ull;
+                            }
+                            tmem_st_pairs<NB>(tm_row + C::A_COL0 + g * C::KA, tm_row + (16u << 16) + C::A_COL0 + g * C::KA, pr);
                             tmem_wait_st();
                         }
                         tc_fence_before();
@@ -461,6 +448,8 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
                         }
                         cp_async_wait1();
                         __syncwarp();
+#pragma unroll
+                        for (int u = 0; u < C::GPW; ++u) wbase[u] = win_ptr(u, bsel);
                     }
                     // a trip in which a chunk of this warp ends, or the item's last
                     // trip, takes the per-row checks; every other trip runs without
@@ -483,6 +472,7 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
                         }
                     }
                 }
+                if (mlow < -(float)EXP_LIMIT) atomicOr(status, ST_ENUMERIC);
             }
             } else {
             if (fast) {

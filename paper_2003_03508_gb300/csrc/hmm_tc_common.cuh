@@ -271,6 +271,105 @@ __device__ __forceinline__ void tmem_st_16x256b(uint32_t taddr, const uint32_t *
     }
 }
 
+// Both 16-lane halves of a warp's quadrant in the 16x256b fragment (t0: lanes
+// 0-15, t1: lanes 16-31 of the quadrant), as 64-bit pairs of adjacent columns:
+// pair h*2NB + 2m + j holds registers 4m + 2j and 4m + 2j + 1 of half h, i.e.
+// row 8j + lane/4 (+16h), columns 8m + 2(lane%4) + {0, 1}. Keeping the data in
+// pairs from the load, through the paired multiplies, to the store lets the
+// register allocator keep each pair in place. The load waits for completion.
+template <int NB>
+__device__ __forceinline__ void tmem_ld_pairs(uint32_t t0, uint32_t t1, unsigned long long *p);
+template <int NB>
+__device__ __forceinline__ void tmem_st_pairs(uint32_t t0, uint32_t t1, const unsigned long long *p);
+
+template <>
+__device__ __forceinline__ void tmem_ld_pairs<4>(uint32_t t0, uint32_t t1, unsigned long long *p) {
+    asm volatile("{\n\t.reg .b32 r<32>;\n\t"
+                 "tcgen05.ld.sync.aligned.16x256b.x4.b32 {r0,r1,r2,r3,r4,r5,r6,r7,r8,r9,r10,r11,r12,r13,r14,r15}, [%16];\n\t"
+                 "tcgen05.ld.sync.aligned.16x256b.x4.b32 {r16,r17,r18,r19,r20,r21,r22,r23,r24,r25,r26,r27,r28,r29,r30,r31}, [%17];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;\n\t"
+                 "mov.b64 %0, {r0, r1};\n\t"
+                 "mov.b64 %1, {r2, r3};\n\t"
+                 "mov.b64 %2, {r4, r5};\n\t"
+                 "mov.b64 %3, {r6, r7};\n\t"
+                 "mov.b64 %4, {r8, r9};\n\t"
+                 "mov.b64 %5, {r10, r11};\n\t"
+                 "mov.b64 %6, {r12, r13};\n\t"
+                 "mov.b64 %7, {r14, r15};\n\t"
+                 "mov.b64 %8, {r16, r17};\n\t"
+                 "mov.b64 %9, {r18, r19};\n\t"
+                 "mov.b64 %10, {r20, r21};\n\t"
+                 "mov.b64 %11, {r22, r23};\n\t"
+                 "mov.b64 %12, {r24, r25};\n\t"
+                 "mov.b64 %13, {r26, r27};\n\t"
+                 "mov.b64 %14, {r28, r29};\n\t"
+                 "mov.b64 %15, {r30, r31};\n\t"
+                 "}"
+                 : "=l"(p[0]), "=l"(p[1]), "=l"(p[2]), "=l"(p[3]), "=l"(p[4]), "=l"(p[5]), "=l"(p[6]), "=l"(p[7]), "=l"(p[8]), "=l"(p[9]), "=l"(p[10]), "=l"(p[11]), "=l"(p[12]), "=l"(p[13]), "=l"(p[14]), "=l"(p[15])
+                 : "r"(t0), "r"(t1) : "memory");
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld_pairs<2>(uint32_t t0, uint32_t t1, unsigned long long *p) {
+    asm volatile("{\n\t.reg .b32 r<16>;\n\t"
+                 "tcgen05.ld.sync.aligned.16x256b.x2.b32 {r0,r1,r2,r3,r4,r5,r6,r7}, [%8];\n\t"
+                 "tcgen05.ld.sync.aligned.16x256b.x2.b32 {r8,r9,r10,r11,r12,r13,r14,r15}, [%9];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;\n\t"
+                 "mov.b64 %0, {r0, r1};\n\t"
+                 "mov.b64 %1, {r2, r3};\n\t"
+                 "mov.b64 %2, {r4, r5};\n\t"
+                 "mov.b64 %3, {r6, r7};\n\t"
+                 "mov.b64 %4, {r8, r9};\n\t"
+                 "mov.b64 %5, {r10, r11};\n\t"
+                 "mov.b64 %6, {r12, r13};\n\t"
+                 "mov.b64 %7, {r14, r15};\n\t"
+                 "}"
+                 : "=l"(p[0]), "=l"(p[1]), "=l"(p[2]), "=l"(p[3]), "=l"(p[4]), "=l"(p[5]), "=l"(p[6]), "=l"(p[7])
+                 : "r"(t0), "r"(t1) : "memory");
+}
+
+template <>
+__device__ __forceinline__ void tmem_st_pairs<4>(uint32_t t0, uint32_t t1, const unsigned long long *p) {
+    asm volatile("{\n\t.reg .b32 r<32>;\n\t"
+                 "mov.b64 {r0, r1}, %2;\n\t"
+                 "mov.b64 {r2, r3}, %3;\n\t"
+                 "mov.b64 {r4, r5}, %4;\n\t"
+                 "mov.b64 {r6, r7}, %5;\n\t"
+                 "mov.b64 {r8, r9}, %6;\n\t"
+                 "mov.b64 {r10, r11}, %7;\n\t"
+                 "mov.b64 {r12, r13}, %8;\n\t"
+                 "mov.b64 {r14, r15}, %9;\n\t"
+                 "mov.b64 {r16, r17}, %10;\n\t"
+                 "mov.b64 {r18, r19}, %11;\n\t"
+                 "mov.b64 {r20, r21}, %12;\n\t"
+                 "mov.b64 {r22, r23}, %13;\n\t"
+                 "mov.b64 {r24, r25}, %14;\n\t"
+                 "mov.b64 {r26, r27}, %15;\n\t"
+                 "mov.b64 {r28, r29}, %16;\n\t"
+                 "mov.b64 {r30, r31}, %17;\n\t"
+                 "tcgen05.st.sync.aligned.16x256b.x4.b32 [%0], {r0,r1,r2,r3,r4,r5,r6,r7,r8,r9,r10,r11,r12,r13,r14,r15};\n\t"
+                 "tcgen05.st.sync.aligned.16x256b.x4.b32 [%1], {r16,r17,r18,r19,r20,r21,r22,r23,r24,r25,r26,r27,r28,r29,r30,r31};\n\t"
+                 "}"
+                 :: "r"(t0), "r"(t1), "l"(p[0]), "l"(p[1]), "l"(p[2]), "l"(p[3]), "l"(p[4]), "l"(p[5]), "l"(p[6]), "l"(p[7]), "l"(p[8]), "l"(p[9]), "l"(p[10]), "l"(p[11]), "l"(p[12]), "l"(p[13]), "l"(p[14]), "l"(p[15]) : "memory");
+}
+
+template <>
+__device__ __forceinline__ void tmem_st_pairs<2>(uint32_t t0, uint32_t t1, const unsigned long long *p) {
+    asm volatile("{\n\t.reg .b32 r<16>;\n\t"
+                 "mov.b64 {r0, r1}, %2;\n\t"
+                 "mov.b64 {r2, r3}, %3;\n\t"
+                 "mov.b64 {r4, r5}, %4;\n\t"
+                 "mov.b64 {r6, r7}, %5;\n\t"
+                 "mov.b64 {r8, r9}, %6;\n\t"
+                 "mov.b64 {r10, r11}, %7;\n\t"
+                 "mov.b64 {r12, r13}, %8;\n\t"
+                 "mov.b64 {r14, r15}, %9;\n\t"
+                 "tcgen05.st.sync.aligned.16x256b.x2.b32 [%0], {r0,r1,r2,r3,r4,r5,r6,r7};\n\t"
+                 "tcgen05.st.sync.aligned.16x256b.x2.b32 [%1], {r8,r9,r10,r11,r12,r13,r14,r15};\n\t"
+                 "}"
+                 :: "r"(t0), "r"(t1), "l"(p[0]), "l"(p[1]), "l"(p[2]), "l"(p[3]), "l"(p[4]), "l"(p[5]), "l"(p[6]), "l"(p[7]) : "memory");
+}
+
 // All MMAs of one group-step (NIMG images of P x NKS slices of K), the first
 // overwriting D, the rest accumulating; B descriptors precomputed.
 template <int PREC, int NIMG, int NKS>

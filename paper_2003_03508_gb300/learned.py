@@ -53,11 +53,24 @@ def esjd(theta_trace: torch.Tensor, scale: torch.Tensor) -> float:
     return float((d * d).sum(dim=2).mean().item())
 
 
+def pcn_pairs(rhos):
+    """(lam, gamma) pairs of the autoregressive family: with the network
+    giving the mean m and spread tau of an independent posterior draw (the
+    cross-chain training target), the proposal theta + lam gamma (m - theta) +
+    lam tau z equals m + rho (theta - m) + sqrt(1 - rho^2) tau z when
+    lam = sqrt(1 - rho^2) and gamma = sqrt((1 - rho) / (1 + rho)): for a
+    Gaussian posterior with that mean and spread it leaves the posterior
+    invariant by itself, so drift and step stay consistent in every dimension
+    (a drift without the matching step size is rejected almost always in
+    hundreds of dimensions)."""
+    return [(float(np.sqrt(1.0 - r * r)), float(np.sqrt((1.0 - r) / (1.0 + r)))) for r in rhos]
+
+
 def fit_learned_proposal(sampler: api.Sampler, theta_trace: torch.Tensor, lag: int = 20, hidden: int = 256,
                          train_steps: int = 2000, batch: int = 512, lr: float = 2e-3, seed: int = 0,
                          target_accept: float = 0.35, pilot_iters: int = 50, lams=(0.8, 0.4, 0.2, 0.1),
                          gamma: float = 0.5, burn: int = 0, select: str = "accept", gammas=None,
-                         cross: bool = False):
+                         cross: bool = False, pairs=None):
     """Train an MLP proposal on a random-walk trace and attach it to `sampler`.
 
     gamma scales the learned drift (the proposal mean is theta + lam s gamma
@@ -67,7 +80,8 @@ def fit_learned_proposal(sampler: api.Sampler, theta_trace: torch.Tensor, lag: i
     acceptance is closest to target_accept, select="esjd" the one with the
     largest expected squared jump distance in units of the history's
     per-coordinate spread. With `gammas` given, the drift factor is searched
-    together with lam (every pair is piloted). Returns (mlp, info) where info
+    together with lam (every pair is piloted); with `pairs` given, exactly
+    those (lam, gamma) pairs are piloted. Returns (mlp, info) where info
     holds the training losses, the chosen lam and gamma, the pilot statistics
     and the wall time spent.
     """
@@ -83,7 +97,10 @@ def fit_learned_proposal(sampler: api.Sampler, theta_trace: torch.Tensor, lag: i
     pilot = {}
     best, best_score = None, None
     spread = X.std(dim=0) + 1e-12
-    grid = [(lam, gamma) for lam in lams] if gammas is None else [(lam, g) for g in gammas for lam in lams]
+    if pairs is not None:
+        grid = list(pairs)
+    else:
+        grid = [(lam, gamma) for lam in lams] if gammas is None else [(lam, g) for g in gammas for lam in lams]
     for lam, gam in grid:
         mlp.set_lambda(lam, gam)
         sampler.set_proposal(mlp)  # rebuild the captured iteration with the new lam
@@ -93,12 +110,12 @@ def fit_learned_proposal(sampler: api.Sampler, theta_trace: torch.Tensor, lag: i
             _, _, _, na1 = sampler.state()
             acc = float((na1 - na0).double().mean().item()) / pilot_iters
             score = esjd(th, spread)
-            pilot[f"{lam:g}/{gam:g}"] = {"accept": acc, "esjd": score}
+            pilot[f"{lam:.4g}/{gam:.4g}"] = {"accept": acc, "esjd": score}
             del th
         else:
             acc = acceptance(sampler, pilot_iters)
             score = -abs(acc - target_accept)
-            pilot[lam if gammas is None else f"{lam:g}/{gam:g}"] = acc
+            pilot[f"{lam:g}/{gam:g}"] = acc
         if best is None or score > best_score:
             best, best_score = (lam, gam), score
     mlp.set_lambda(best[0], best[1])
