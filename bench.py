@@ -29,8 +29,10 @@ Also reported on the same line:
   mcmc          effective samples per second of the log posterior and of
                 label-invariant summaries: the random-walk sampler, the learned
                 (MLP) proposal trained on the random walk's own history, and
-                the t-walk, same chains and iterations (K=16, 512 chains; T
-                reduced so the run stays within about a minute).
+                the t-walk, same chains and iterations (K=16, 512 chains,
+                T=2^20: the learned-proposal workload; 1000 measured iterations
+                per sampler after a shortened burn-in so the leg stays within
+                a few minutes).
 
 ``--impl reference`` times the CPU oracle instead (rank 0 only).
 Multi-GPU (torchrun): every rank evaluates its own n_prop proposals (weak
@@ -79,9 +81,11 @@ def parse():
     ap.add_argument("--runlen-min", type=int, default=4)
     ap.add_argument("--no-peaks", action="store_true")
     ap.add_argument("--mcmc-K", type=int, default=16)
-    ap.add_argument("--mcmc-T", type=int, default=16384)
+    ap.add_argument("--mcmc-T", type=int, default=1 << 20)
     ap.add_argument("--mcmc-chains", type=int, default=512)
-    ap.add_argument("--mcmc-iters", type=int, default=10000)
+    ap.add_argument("--mcmc-iters", type=int, default=1000)
+    ap.add_argument("--mcmc-burn", type=int, default=600)
+    ap.add_argument("--mcmc-precision", default="tf32_split")
     return ap.parse_args()
 
 
@@ -503,12 +507,13 @@ def main():
 
     if rank == 0 and not args.no_mcmc:
         from paper_2003_03508_gb300 import chains
-        mopts = api.make_opts(precision="tf32", recheck_fp32=1)
+        mopts = api.make_opts(precision=args.mcmc_precision, recheck_fp32=1)
         result["mcmc"] = chains.rw_vs_learned(K=args.mcmc_K, T=args.mcmc_T, chains=args.mcmc_chains,
-                                              seed=args.seed, n_measure=args.mcmc_iters, opts=mopts)
-        result["mcmc"]["likelihood"] = ("tf32 tensor cores for every Metropolis-Hastings ratio; the chains' "
-                                        "current states (their last accepted proposals) re-evaluated in fp32 "
-                                        "at the end of each call into a separate report")
+                                              seed=args.seed, n_measure=args.mcmc_iters, opts=mopts,
+                                              burn=args.mcmc_burn, pilot_iters=50, tune_burn=100, tune_iters=50)
+        result["mcmc"]["likelihood"] = (f"{args.mcmc_precision} tensor cores for every Metropolis-Hastings ratio; "
+                                        "the chains' current states (their last accepted proposals) re-evaluated "
+                                        "in fp32 at the end of each call into a separate report")
 
     if rank == 0 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1

@@ -90,7 +90,8 @@ def _ess_summary(lp, summ, K):
 def rw_vs_learned(K=16, T=16384, chains=512, seed=0, burn=3000, history=200, lag=20, hidden=256,
                   train_steps=2000, batch=512, lr=2e-3, n_measure=1000, alpha_P=0.5,
                   target_accept=0.25, opts=None, cross=True, pilot_iters=100,
-                  pcn_rhos=(0.9, 0.97, 0.99, 0.995, 0.998), rw_lams=(0.25, 0.12, 0.06)):
+                  pcn_rhos=(0.9, 0.97, 0.99, 0.995, 0.998), rw_lams=(0.25, 0.12, 0.06),
+                  tune_burn=200, tune_iters=100):
     """Tune and burn in the random walk, train the learned proposal on its
     history (cross=True: pairs of different chains at the same iteration,
     else pairs `lag` iterations apart in one chain), pick its step factor and
@@ -100,9 +101,12 @@ def rw_vs_learned(K=16, T=16384, chains=512, seed=0, burn=3000, history=200, lag
     report effective samples per second of the log posterior and of the
     label-invariant summaries (Geyer initial monotone sequence estimator,
     summed over chains)."""
-    prob = tremor_problem(K, T, chains, seed)
+    # the posterior narrows like 1/sqrt(T): start the chains and the step
+    # search at that scale (the defaults were set at T = 16384)
+    shrink = min(1.0, math.sqrt(16384.0 / T))
+    prob = tremor_problem(K, T, chains, seed, spread=0.01 * shrink)
     pr = api.make_prior(K, alpha_P=alpha_P)
-    step0 = base_steps(K)
+    step0 = base_steps(K) * shrink
 
     def make(th, step, s):
         return api.Sampler(K, th.contiguous(), torch.from_numpy(step).cuda(), s, [0, T], prob["xy"],
@@ -115,8 +119,8 @@ def rw_vs_learned(K=16, T=16384, chains=512, seed=0, burn=3000, history=200, lag
     mult = 1.0
     while mult >= 1.0 / 256:
         s = make(prob["theta0"], step0 * mult, seed + 1)
-        s.step(200)
-        acc = learned.acceptance(s, 100)
+        s.step(tune_burn)
+        acc = learned.acceptance(s, tune_iters)
         s.close()
         if best is None or abs(acc - target_accept) < abs(best[1] - target_accept):
             best = (mult, acc)
@@ -165,8 +169,9 @@ def rw_vs_learned(K=16, T=16384, chains=512, seed=0, burn=3000, history=200, lag
     finite = bool(torch.isfinite(lp_ml).all().item() and torch.isfinite(lp_rw).all().item())
     out = {
         "K": K, "T": T, "chains": chains, "theta_dim": api.theta_dim(K), "iterations": n_measure,
+        "burn_in": burn, "history": history, "step_scale": shrink,
         "rw": {"ess": e_rw, "seconds": t_rw, "ess_per_s": e_rw / t_rw, "accept": acc_rw,
-               "step_mult": best[0], "ms_per_iter": 1e3 * t_rw / n_measure,
+               "step_mult": best[0] * shrink, "ms_per_iter": 1e3 * t_rw / n_measure,
                "ess_summaries_min": s_rw["summaries_min"], "ess_summaries_median": s_rw["summaries_median"]},
         "learned": {"ess": e_ml, "seconds": t_ml, "ess_per_s": e_ml / t_ml, "accept": acc_ml,
                     "lam": info["lam"], "gamma": info["gamma"], "hidden": hidden, "lam_pilots": info["pilot"],

@@ -1,14 +1,23 @@
 """Parity of the tensor-core (tcgen05) chunk products with the FP64 oracle.
 
-Tolerance for TF32 / BF16 / TF32-split chunk products: |d| <= 1e-4 |log L|
-(relative in log L), or, for short sequences whose |log L| is small, the
-per-T absolute bound |d| <= 8 sqrt(T) u (u = 2^-11 for TF32 operands, 2^-9
-for BF16), plus 1e-3. The error budget behind it: the running product is
-rounded to the operand type every step (round to nearest, unbiased, so the
-errors add up like a random walk: O(sqrt(T) u) in log L), and P is rounded
-once (a bias of at most ~T u / sqrt(K) in log L; removed to O(u^2) by the
-hi+lo split used for BF16 and TF32-split). Each test also reports the
-observed error so the per-dtype figures can be read off the log.
+Tolerance, per precision, an absolute bound in log L that grows with the
+number of steps T (u: the operand's unit roundoff, 2^-11 for TF32, 2^-8 for
+BF16):
+
+* TF32-split (P carried as hi + lo, the running product rounded to nearest
+  every step): |d| <= 8 sqrt(T) u. The per-step roundings are unbiased, so
+  they add up like a random walk; P's own rounding error is O(u^2).
+* TF32 (P rounded once): |d| <= 8 sqrt(T) u + T u / sqrt(K). Rounding P once
+  changes every row sum of P by up to ~u / sqrt(K), a bias of that size per
+  step. (The running product is truncated by the tensor core and the mean
+  loss compensated in the emissions; what is left behaves like rounding.)
+* BF16 (P as hi + lo, the running product in BF16): |d| <= 8 sqrt(T) u +
+  4 T u^2, the second term an empirical allowance for the drift seen at long
+  T (35 nats at T = 2^20, K = 32, both on the GPU and in a numpy replay of
+  the kernels' rounding).
+
+Full-size cases assert both this bound and the benchmark spec's relative bar,
+|d| <= 1e-4 |log L|. Each test prints the observed error.
 """
 import math
 
@@ -23,12 +32,26 @@ pytestmark = pytest.mark.gpu
 
 TC_REL, TC_ABS = 1e-4, 1e-3
 PRECS = ["tf32", "tf32_split", "bf16"]
-UNIT = {"tf32": 2.0 ** -11, "tf32_split": 2.0 ** -11, "bf16": 2.0 ** -9}
+UNIT = {"tf32": 2.0 ** -11, "tf32_split": 2.0 ** -11, "bf16": 2.0 ** -8}
 
 
-def tol(prec, T, ref):
-    """Allowed |log L error| for a tensor-core precision on T observations."""
-    return max(TC_REL * abs(ref), 8.0 * math.sqrt(max(T, 1)) * UNIT[prec]) + TC_ABS
+def tol(prec, T, K):
+    """Allowed |log L error| for a tensor-core precision on T observations, K states."""
+    u = UNIT[prec]
+    b = 8.0 * math.sqrt(max(T, 1)) * u
+    if prec == "tf32":
+        b += T * u / math.sqrt(K)
+    elif prec == "bf16":
+        b += 4.0 * T * u * u
+    return b + TC_ABS
+
+
+def check_full(prec, T, K, got, ref):
+    """Both bounds at full size: the per-T absolute one and the relative bar."""
+    got, ref = np.asarray(got, np.float64), np.asarray(ref, np.float64)
+    err = np.abs(got - ref)
+    assert np.all(err <= tol(prec, T, K)), (prec, err.max(), tol(prec, T, K))
+    assert np.all(err <= TC_REL * np.abs(ref)), (prec, (err / np.abs(ref)).max())
 
 
 def _run(api, prm, xy, tremor, **opt):
@@ -51,7 +74,7 @@ def test_tc_parity_sizes(cuda_lib, K, prec):
         got = _run(cuda_lib, prm, obs.xy, obs.tremor, precision=prec, chunk_len=L)
         err = abs(got - ref)
         print(f"K={K} {prec} L={L}: rel err {err / abs(ref):.2e}")
-        assert err <= tol(prec, T, ref), (K, prec, L, got, ref)
+        assert err <= tol(prec, T, K), (K, prec, L, got, ref)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -62,7 +85,7 @@ def test_tc_small_T(cuda_lib, prec, T):
     obs = synth.sample_observations(prm, T, rng)
     ref = oracle.loglik(prm, obs.xy, obs.tremor)
     got = _run(cuda_lib, prm, obs.xy, obs.tremor, precision=prec, chunk_len=64)
-    assert abs(got - ref) <= tol(prec, T, ref), (T, got, ref)
+    assert abs(got - ref) <= tol(prec, T, 9), (T, got, ref)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -74,7 +97,7 @@ def test_tc_wide_small_T(cuda_lib, prec, K, T):
     obs = synth.sample_observations(prm, T, rng)
     ref = oracle.loglik(prm, obs.xy, obs.tremor)
     got = _run(cuda_lib, prm, obs.xy, obs.tremor, precision=prec, chunk_len=64)
-    assert abs(got - ref) <= tol(prec, T, ref), (K, T, got, ref)
+    assert abs(got - ref) <= tol(prec, T, K), (K, T, got, ref)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -89,6 +112,11 @@ def test_tc_batched_segments(cuda_lib, prec, K):
     ref = oracle.loglik_batched(d["params"], d["xy"], d["tremor"], d["offsets"], n_threads=4)
     rel = np.abs(got - ref) / np.abs(ref)
     print(f"K={K} {prec} batched max rel err {rel.max():.2e}")
+    Ts = np.diff(d["offsets"])
+    for q in range(len(ref)):
+        # per-segment bounds add up over the segments of one proposal
+        bound = sum(tol(prec, int(t), K) for t in Ts)
+        assert abs(got[q] - ref[q]) <= bound, (q, got[q] - ref[q], bound)
     assert np.all(rel <= TC_REL), rel
 
 
@@ -116,7 +144,7 @@ def test_tc_k25_t2p20(cuda_lib):
     for prec in PRECS:
         got = _run(cuda_lib, d["params"], d["xy"], d["tremor"], precision=prec)
         print(f"K=25 T=2^20 {prec}: rel err {abs(got - ref) / abs(ref):.2e}, abs {abs(got - ref):.3f}")
-        assert abs(got - ref) <= TC_REL * abs(ref)
+        check_full(prec, len(d["tremor"]), 25, got, ref)
 
 
 def test_bench_workload_sampled(cuda_lib):
@@ -136,7 +164,7 @@ def test_bench_workload_sampled(cuda_lib):
     sub = type(d["params"])(*(a[pick] for a in d["params"].as_tuple()))
     ref = oracle.loglik_batched(sub, d["xy"], d["tremor"], d["offsets"], n_threads=4)
     print("sampled rel err tf32", np.abs(tc[pick] - ref) / np.abs(ref), "fp32", np.abs(fp[pick] - ref) / np.abs(ref))
-    assert np.all(np.abs(tc[pick] - ref) <= TC_REL * np.abs(ref))
+    check_full("tf32", 1 << 20, 32, tc[pick], ref)
     assert np.all(np.abs(fp[pick] - ref) <= 1e-6 * np.abs(ref))
 
 
@@ -162,7 +190,10 @@ def test_precision_sweep_wide_full_size(cuda_lib, K):
     for prec, v in res.items():
         rel = np.abs(v[pick] - ref) / np.abs(ref)
         print(f"K={K} T=2^22 {prec}: sampled rel err {rel.max():.2e}")
-        assert np.all(rel <= (1e-6 if prec == "fp32" else TC_REL)), (prec, rel)
+        if prec == "fp32":
+            assert np.all(rel <= 1e-6), (prec, rel)
+        else:
+            check_full(prec, 1 << 22, K, v[pick], ref)
         if prec != "fp32":
             assert np.all(np.abs(v - res["fp32"]) <= TC_REL * np.abs(res["fp32"]))
 
@@ -190,4 +221,7 @@ def test_uneven_segments_full_size(cuda_lib):
     print("64 segments, 2^24 steps: rel err fp32", np.abs(fp[pick] - ref) / np.abs(ref),
           "tf32", np.abs(tc[pick] - ref) / np.abs(ref))
     assert np.all(np.abs(fp[pick] - ref) <= 1e-6 * np.abs(ref))
+    Ts = np.diff(d["offsets"])
+    bound = sum(tol("tf32", int(t), 32) for t in Ts)
+    assert np.all(np.abs(tc[pick] - ref) <= bound), (np.abs(tc[pick] - ref), bound)
     assert np.all(np.abs(tc[pick] - ref) <= TC_REL * np.abs(ref))
