@@ -30,7 +30,7 @@ Also reported on the same line:
                 label-invariant summaries: the random-walk sampler, the learned
                 (MLP) proposal trained on the random walk's own history, and
                 the t-walk, same chains and iterations (K=16, 512 chains,
-                T=2^20: the learned-proposal workload; 1000 measured iterations
+                T=2^20: the learned-proposal workload; 600 measured iterations
                 per sampler after a shortened burn-in so the leg stays within
                 a few minutes).
 
@@ -83,8 +83,8 @@ def parse():
     ap.add_argument("--mcmc-K", type=int, default=16)
     ap.add_argument("--mcmc-T", type=int, default=1 << 20)
     ap.add_argument("--mcmc-chains", type=int, default=512)
-    ap.add_argument("--mcmc-iters", type=int, default=1000)
-    ap.add_argument("--mcmc-burn", type=int, default=600)
+    ap.add_argument("--mcmc-iters", type=int, default=600)
+    ap.add_argument("--mcmc-burn", type=int, default=400)
     ap.add_argument("--mcmc-precision", default="tf32_split")
     return ap.parse_args()
 
@@ -510,7 +510,8 @@ def main():
         mopts = api.make_opts(precision=args.mcmc_precision, recheck_fp32=1)
         result["mcmc"] = chains.rw_vs_learned(K=args.mcmc_K, T=args.mcmc_T, chains=args.mcmc_chains,
                                               seed=args.seed, n_measure=args.mcmc_iters, opts=mopts,
-                                              burn=args.mcmc_burn, pilot_iters=50, tune_burn=100, tune_iters=50)
+                                              burn=args.mcmc_burn, pilot_iters=30, tune_burn=100, tune_iters=50,
+                                              train_steps=1000)
         result["mcmc"]["likelihood"] = (f"{args.mcmc_precision} tensor cores for every Metropolis-Hastings ratio; "
                                         "the chains' current states (their last accepted proposals) re-evaluated "
                                         "in fp32 at the end of each call into a separate report")

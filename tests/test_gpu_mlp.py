@@ -202,8 +202,9 @@ def test_learned_sampler_full_size(cuda_lib):
     """The learned-proposal workload's launch: K=16 (d=351), T=2^20, 512
     chains, TF32 likelihood with FP32 recheck, a 2x256 network. A few random-
     walk iterations, a short training run on their trace, then learned
-    iterations; the stored log likelihood of sampled chains is the FP64
-    oracle's, and the stored log posterior is that plus the prior."""
+    iterations; the FP32 recheck of sampled chains' states matches the FP64
+    oracle, the stored (TF32) log likelihood is within TF32's tolerance of
+    it, and the stored log posterior is that plus the prior."""
     api = cuda_lib
     from paper_2003_03508_gb300 import chains
     K, T, C = 16, 1 << 20, 512
@@ -229,6 +230,10 @@ def test_learned_sampler_full_size(cuda_lib):
     prm = synth.HMMParams(*(t[pick].cpu().numpy() for t in (pi, P, p, mu, cov)))
     ref = oracle.loglik_batched(prm, prob["obs"].xy, prob["obs"].tremor, np.array([0, T], np.int64), n_threads=2)
     got = ll[pick].cpu().numpy()
-    print("K=16 T=2^20 512 chains: stored log L rel err vs oracle", np.abs(got - ref) / np.abs(ref))
-    assert np.all(np.abs(got - ref) <= 1e-6 * np.abs(ref))
+    rep = s.fp32_report()[0][pick].cpu().numpy()
+    print("K=16 T=2^20 512 chains: stored (TF32) log L rel err vs oracle", np.abs(got - ref) / np.abs(ref),
+          "FP32 report", np.abs(rep - ref) / np.abs(ref))
+    # the stored values are the sampler's TF32 ones; the recheck reports FP32
+    assert np.all(np.abs(got - ref) <= 1e-4 * np.abs(ref))
+    assert np.all(np.abs(rep - ref) <= 1e-6 * np.abs(ref))
     s.close(); m.close()
