@@ -633,6 +633,18 @@ int hmm_sampler_set_twalk(hmm_sampler *sampler, const float *theta2, void *strea
 int hmm_sampler_twalk_state(hmm_sampler *sampler, float *theta2_out, double *logpost2_out, void *stream);
 
 /*
+ * Failure-detection check (the paper has no counterpart): runs, on `device`,
+ * one bounded wait of the kind every tensor-core kernel uses on its
+ * mbarriers, on a barrier phase that nothing completes, with a limit of
+ * limit_ms (0 < limit_ms <= 2000) measured in cycles at the rated clock.
+ * Returns HMM_ETIMEOUT when the wait gave up, set the status bit and let the
+ * kernel finish (the expected outcome), HMM_OK or HMM_EINVAL if it did not,
+ * HMM_ECUDA on a runtime error. *waited_ms (host, may be NULL) receives the
+ * time waited. Allocates two small buffers; synchronises the device.
+ */
+int hmm_check_bounded_wait(int device, double limit_ms, double *waited_ms);
+
+/*
  * Measured FP32 FFMA throughput of `device` in TFLOP/s (written to *tflops,
  * a host pointer): the roofline denominator of the FP32-SIMT chunk kernel,
  * from a kernel of independent FFMA chains timed with CUDA events (best of

@@ -143,6 +143,7 @@ SIGNATURES = {
     "hmm_sampler_set_twalk": (ctypes.c_int, [_VP, _VP, _VP]),
     "hmm_sampler_twalk_state": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "hmm_loglik_noalloc": (ctypes.c_int, [ctypes.POINTER(hmm_params), ctypes.POINTER(hmm_obs), _VP, _VP]),
+    "hmm_check_bounded_wait": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
     "hmm_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "hmm_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int)]),
@@ -793,3 +794,10 @@ def measure_fp32_peak(device: int = 0) -> float:
     if rc != HMM_OK:
         raise HMMError(rc, "hmm_measure_fp32_peak failed")
     return float(v.value)
+
+
+def check_bounded_wait(limit_ms: float = 20.0, device: int = 0):
+    """Run the device-side bounded-wait check; returns (status code, ms waited)."""
+    w = ctypes.c_double(0.0)
+    rc = load_library().hmm_check_bounded_wait(int(device), float(limit_ms), ctypes.byref(w))
+    return int(rc), float(w.value)

@@ -71,13 +71,13 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
 // CTA's abort flag and the ETIMEOUT status bit) if it runs out, or at once
 // if another warp already aborted.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
-                                          unsigned *status) {
+                                          unsigned *status, long long limit = SPIN_LIMIT_CYCLES) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (clock64() - t0 > SPIN_LIMIT_CYCLES) {
+        if (clock64() - t0 > limit) {
             *abort_flag = 1;
             atomicOr(status, ST_ETIMEOUT);
             return false;
