@@ -266,12 +266,10 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
                 cp_async_commit();
             }
 
-            // The fast path covers the default renormalisation interval with
-            // TF32 operands (BF16 packs two operands per TMEM column, which the
-            // 16x256b fragment below does not match).
-            const bool fast = (renorm == FAST_R) && (PREC != HMM_PREC_BF16 || steps % FAST_R == 0);
+            // The fast path covers the default renormalisation interval for every
+            // tensor-core precision; the general path below takes any other.
+            const bool fast = (renorm == FAST_R);
             bool bad = false;
-            if constexpr (PREC != HMM_PREC_BF16) {
             if (fast) {
                 // ---- fast path: trips of four steps, renormalisation on the fourth ----
                 // TMEM is read and written in the 16x256b fragment, kept as
@@ -418,12 +416,18 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
                             // next A operand (TF32: the raw FP32 bits, truncated by the
                             // tensor core; TF32-split: rounded to nearest first, both
                             // halves of a pair in one add: values are non-negative, so
-                            // the low half never carries)
-                            if constexpr (!TRUNC) {
+                            // the low half never carries; BF16: rounded to nearest and
+                            // packed two per column)
+                            const uint32_t a0 = tm_row + C::A_COL0 + g * C::KA, a1 = a0 + (16u << 16);
+                            if constexpr (PREC == HMM_PREC_BF16) {
+                                tmem_st_bf16_pairs<NB>(a0, a1, pr);
+                            } else {
+                                if constexpr (!TRUNC) {
 #pragma unroll
-                                for (int k = 0; k < NP; ++k) pr[k] += 0x0000100000001000ull;
+                                    for (int k = 0; k < NP; ++k) pr[k] += 0x0000100000001000ull;
+                                }
+                                tmem_st_pairs<NB>(a0, a1, pr);
                             }
-                            tmem_st_pairs<NB>(tm_row + C::A_COL0 + g * C::KA, tm_row + (16u << 16) + C::A_COL0 + g * C::KA, pr);
                             tmem_wait_st();
                         }
                         tc_fence_before();
@@ -473,100 +477,6 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
                     }
                 }
                 if (mlow < -(float)EXP_LIMIT) atomicOr(status, ST_ENUMERIC);
-            }
-            } else {
-            if (fast) {
-                // ---- BF16 fast path: four steps per trip, renormalisation on the fourth ----
-                for (int t0 = 0; t0 < steps && !bad; t0 += FAST_R) {
-                    const int bsel = (t0 / C::WIN) & 1;
-                    if ((t0 & (C::WIN - 1)) == 0) {
-                        if (t0 > 0) {
-#pragma unroll
-                            for (int u = 0; u < C::GPW; ++u) {
-#pragma unroll
-                                for (int v = 0; v < C::NWIN; ++v) {
-                                    const int s = t0 + C::WIN + jl + KP * v;
-                                    if (s < len[u]) cp_async8(smem_u32(win_ptr(u, bsel ^ 1) + jl + KP * v), packed + pstart[u] + s);
-                                }
-                            }
-                            cp_async_commit();
-                        }
-                        cp_async_wait1();
-                        __syncwarp();
-                    }
-#pragma unroll
-                    for (int r = 0; r < FAST_R; ++r) {
-                        const int t = t0 + r;
-                        const int w = (t0 & (C::WIN - 1)) + r;
-                        int Et[C::GPW];
-#pragma unroll
-                        for (int u = 0; u < C::GPW; ++u) {
-                            const float2 o = win_ptr(u, bsel)[w];
-                            const float dx = o.x - mux, dy = o.y - muy;
-                            float l = fmaf(qa * dx, dx, fmaf(qb * dx, dy, fmaf(qc * dy, dy, ctr)));
-                            l = isnan(o.x) ? cno : l;
-                            const float m = chunk_max<KP>(l, lane);
-                            float mf;
-                            const int e = round_to_int(m, mf);
-                            const bool ok = m >= -(float)EXP_LIMIT;
-                            Et[u] = ok ? e : 0;
-                            const float d = ex2_approx(l - mf);
-                            if (!ok && m != -INFINITY && t < len[u]) atomicOr(status, ST_ENUMERIC);
-                            sD[u * 32 + lane] = ok ? d : 0.0f;
-                        }
-                        __syncwarp();
-#pragma unroll
-                        for (int u = 0; u < C::GPW; ++u) {
-                            const int g = team + E * u;
-                            if (!(glive >> u & 1u)) continue;
-                            const bool okw = __all_sync(0xffffffffu, mbar_wait(&full[g], (full_par >> g) & 1u, abort_flag, status));
-                            full_par ^= 1u << g;
-                            if (!okw) {
-                                bad = true;
-                                break;
-                            }
-                            tc_fence_after();
-                            float a[KP];
-                            tmem_ld_row<KP>(tm_row + g * KP, a);
-                            tmem_wait_ld();
-                            scale_row<KP>(a, sD + u * 32 + half * KP);
-                            expo[u] += Et[u];
-                            float mx = 1.0f;
-                            if (r == FAST_R - 1) mx = renorm_row<KP>(a, expo[u], t < len[u], status);
-                            if (t + 1 == len[u]) {
-                                // this lane's chunk ends here: renormalise (if not done) and write it
-                                if (r != FAST_R - 1) mx = renorm_row<KP>(a, expo[u], true, status);
-                                const size_t jj = (size_t)q * n_chunks + (size_t)b * per_item + g * C::CPG + cs;
-                                float4 *dst = reinterpret_cast<float4 *>(A0 + jj * KP * KP + (size_t)i * KP);
-#pragma unroll
-                                for (int j4 = 0; j4 < KP / 4; ++j4)
-                                    dst[j4] = make_float4(a[4 * j4], a[4 * j4 + 1], a[4 * j4 + 2], a[4 * j4 + 3]);
-                                e0[jj * KP + i] = (mx > 0.0f) ? expo[u] : ZERO_ROW_EXP32;
-                            }
-                            if (t + 1 < steps) {
-                                // next A operand row (finished chunks' rows carry values nobody reads)
-                                uint32_t *wv = reinterpret_cast<uint32_t *>(a);
-                                if constexpr (C::ESZ == 4) {
-#pragma unroll
-                                    for (int c = 0; c < KP; ++c) wv[c] = to_tf32_bits(a[c]);
-                                } else {
-#pragma unroll
-                                    for (int c = 0; c < KP / 2; ++c) {
-                                        __nv_bfloat162 bb = __floats2bfloat162_rn(a[2 * c], a[2 * c + 1]);
-                                        wv[c] = *reinterpret_cast<uint32_t *>(&bb);
-                                    }
-                                }
-                                tmem_st_row<C::KA>(tm_row + C::A_COL0 + g * C::KA, wv);
-                                tmem_wait_st();
-                                tc_fence_before();
-                                __syncwarp();
-                                if (lane == 0) mbar_arrive(&empty[g]);
-                            }
-                        }
-                        if (bad) break;
-                    }
-                }
-            }
             }
             int rcount = renorm;
             for (int t = 0; t < steps && !fast; ++t) {

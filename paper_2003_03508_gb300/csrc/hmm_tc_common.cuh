@@ -447,6 +447,39 @@ __device__ __forceinline__ float max3f(float a, float b, float c) {
     return r;
 }
 
+// The same pairs rounded to BF16 and stored as the BF16 A operand (two
+// K-adjacent elements per 32-bit TMEM column, the even one in the low half):
+// pair h*2NB + 2m + j (row 8j + lane/4 + 16h, columns 8m + 2(lane%4) + {0, 1})
+// becomes the word at column 4m + lane%4 of that row, which is register
+// 2m + j of the 16x128b fragment (thread t: lane t/4 and t/4 + 8, column t%4
+// of each 4-column repetition).
+template <int NB>
+__device__ __forceinline__ void tmem_st_bf16_pairs(uint32_t t0, uint32_t t1, const unsigned long long *p) {
+    static_assert(NB == 2 || NB == 4, "16x128b repetitions");
+    uint32_t w[4 * NB];
+#pragma unroll
+    for (int k = 0; k < 4 * NB; ++k) {
+        float a0, a1;
+        unpack2(p[k], a0, a1);
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w[k]) : "f"(a1), "f"(a0));
+    }
+    if constexpr (NB == 4) {
+        asm volatile("tcgen05.st.sync.aligned.16x128b.x4.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(t0), "r"(w[0]),
+                     "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                     : "memory");
+        asm volatile("tcgen05.st.sync.aligned.16x128b.x4.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(t1), "r"(w[8]),
+                     "r"(w[9]), "r"(w[10]), "r"(w[11]), "r"(w[12]), "r"(w[13]), "r"(w[14]), "r"(w[15])
+                     : "memory");
+    } else {
+        asm volatile("tcgen05.st.sync.aligned.16x128b.x2.b32 [%0], {%1,%2,%3,%4};" ::"r"(t0), "r"(w[0]), "r"(w[1]),
+                     "r"(w[2]), "r"(w[3])
+                     : "memory");
+        asm volatile("tcgen05.st.sync.aligned.16x128b.x2.b32 [%0], {%1,%2,%3,%4};" ::"r"(t1), "r"(w[4]), "r"(w[5]),
+                     "r"(w[6]), "r"(w[7])
+                     : "memory");
+    }
+}
+
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
 }

@@ -149,23 +149,45 @@ def test_tc_k25_t2p20(cuda_lib):
 
 def test_bench_workload_sampled(cuda_lib):
     """K=32, T=2^20, 256 proposals, automatic chunking (the benchmark's launch):
-    TF32 against the oracle on sampled proposals, and against FP32-SIMT on all."""
+    every tensor-core precision against the oracle on sampled proposals, and
+    against FP32-SIMT on all."""
     api = cuda_lib
     d = synth.batched_inputs(K=32, T=1 << 20, n_prop=256, seed=3)
     ctx = api.default_context()
     dev = api.to_device(d["params"])
     xy = torch.from_numpy(d["xy"]).cuda()
     fl = torch.from_numpy(d["tremor"]).cuda()
-    tc = ctx.hmm_loglik_batched(*dev, d["offsets"], xy, fl, opts=api.make_opts(precision="tf32")).cpu().numpy()
     fp = ctx.hmm_loglik_batched(*dev, d["offsets"], xy, fl, opts=api.make_opts(precision="fp32")).cpu().numpy()
     assert ctx.hmm_status() == api.HMM_OK
-    assert np.all(np.abs(tc - fp) <= TC_REL * np.abs(fp))
+    tc = {}
+    for prec in PRECS:
+        tc[prec] = ctx.hmm_loglik_batched(*dev, d["offsets"], xy, fl,
+                                          opts=api.make_opts(precision=prec)).cpu().numpy()
+        assert ctx.hmm_status() == api.HMM_OK
+        assert np.all(np.abs(tc[prec] - fp) <= TC_REL * np.abs(fp)), prec
     pick = [0, 77, 200, 255]
     sub = type(d["params"])(*(a[pick] for a in d["params"].as_tuple()))
     ref = oracle.loglik_batched(sub, d["xy"], d["tremor"], d["offsets"], n_threads=4)
-    print("sampled rel err tf32", np.abs(tc[pick] - ref) / np.abs(ref), "fp32", np.abs(fp[pick] - ref) / np.abs(ref))
-    check_full("tf32", 1 << 20, 32, tc[pick], ref)
+    print("sampled rel err fp32", np.abs(fp[pick] - ref) / np.abs(ref))
     assert np.all(np.abs(fp[pick] - ref) <= 1e-6 * np.abs(ref))
+    for prec, v in tc.items():
+        print(f"sampled rel err {prec}", np.abs(v[pick] - ref) / np.abs(ref))
+        check_full(prec, 1 << 20, 32, v[pick], ref)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("K", [16, 32])
+@pytest.mark.parametrize("R", [1, 3, 8])
+def test_tc_renorm_intervals(cuda_lib, prec, K, R):
+    """Renormalisation intervals other than the fast path's four (the general
+    per-row path), ragged chunk tails included, against the oracle."""
+    rng = np.random.default_rng(4100 + 10 * K + R)
+    prm = synth.random_params(K, rng)
+    T = 5000 + 37
+    obs = synth.sample_observations(prm, T, rng)
+    ref = oracle.loglik(prm, obs.xy, obs.tremor)
+    got = _run(cuda_lib, prm, obs.xy, obs.tremor, precision=prec, chunk_len=256, renorm_every=R)
+    assert abs(got - ref) <= tol(prec, T, K), (K, prec, R, got, ref)
 
 
 @pytest.mark.parametrize("K", [64, 80])
