@@ -258,6 +258,29 @@ int hmm_last_launch_count(const hmm_ctx *ctx);
  */
 int hmm_last_chunk_len(const hmm_ctx *ctx);
 
+/*
+ * Graph replay of the batched call (the schedule of Section "The likelihood
+ * algorithm" as one CUDA graph; the paper has no counterpart). With it on
+ * (the default), hmm_loglik_batched (and hmm_loglik) captures its launch
+ * sequence into a CUDA graph on a stream of the context's own and launches
+ * the graph into the caller's stream; a later call with the same shape,
+ * segment offsets, options, parameter/observation/output pointers and
+ * workspace replays that graph instead of launching the kernels one by one.
+ * The inputs' contents may change between calls (the kernels read them when
+ * the graph runs). Calls made while the caller's stream is itself being
+ * captured, and calls with phase profiling on, launch directly. Results are
+ * identical either way. `on` = 0 turns it off (and frees the graph);
+ * returns HMM_OK or HMM_EINVAL for a null context.
+ */
+int hmm_set_call_graphs(hmm_ctx *ctx, int on);
+
+/*
+ * How the last hmm_loglik / hmm_loglik_batched call ran: 0 = kernels launched
+ * directly, 1 = captured into a new graph and launched, 2 = an existing graph
+ * replayed; -1 for a null context.
+ */
+int hmm_last_call_graph(const hmm_ctx *ctx);
+
 /* ---- chunk-length tuning of the batched schedule ----
  *
  * Section "The likelihood algorithm" splits the matrix chain into chunks

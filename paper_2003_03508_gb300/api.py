@@ -102,6 +102,8 @@ SIGNATURES = {
                                                _VP, _VP, _VP, ctypes.POINTER(hmm_opts), _VP, _VP]),
     "hmm_last_launch_count": (ctypes.c_int, [_VP]),
     "hmm_last_chunk_len": (ctypes.c_int, [_VP]),
+    "hmm_set_call_graphs": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "hmm_last_call_graph": (ctypes.c_int, [_VP]),
     "hmm_default_chunk_len": (ctypes.c_int32, [_I32, _I32, _I32, ctypes.c_int64, _I32]),
     "hmm_tune_candidates": (ctypes.c_int, [_I32, _I32, _I32, ctypes.c_int64, _I32, _VP, _I32,
                                            ctypes.POINTER(_I32)]),
@@ -237,6 +239,16 @@ class Context:
     @property
     def last_chunk_len(self) -> int:
         return int(self.lib.hmm_last_chunk_len(self.h))
+
+    def set_call_graphs(self, on: bool = True):
+        """Capture and replay the batched call as a CUDA graph (default on)."""
+        self._check(self.lib.hmm_set_call_graphs(self.h, int(bool(on))))
+
+    @property
+    def last_call_graph(self) -> int:
+        """0: the last call launched its kernels directly; 1: it captured a
+        new graph and launched it; 2: it replayed the existing graph."""
+        return int(self.lib.hmm_last_call_graph(self.h))
 
     def hmm_profile_enable(self, on: bool = True):
         self._check(self.lib.hmm_profile_enable(self.h, int(bool(on))))

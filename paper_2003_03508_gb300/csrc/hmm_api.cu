@@ -74,7 +74,23 @@ struct hmm_ctx {
     cudaEvent_t ev[HMM_PHASE_COUNT + 1] = {};
     double prof_ms[HMM_PHASE_COUNT] = {};
     int prof_calls = 0;
+    // the batched call's launch sequence as an instantiated CUDA graph
+    bool graphs_on = true;
+    cudaStream_t cap_stream = nullptr;  // captures run here: the legacy default stream cannot be captured
+    cudaGraphExec_t call_exec = nullptr;
+    std::vector<uint64_t> call_key;     // what the graph's launches depend on
+    std::vector<uint64_t> seen_key;     // the previous direct call's (a repeat is captured)
+    int call_launches = 0;
+    int last_graph = 0;                 // 0 direct, 1 captured and launched, 2 replayed
+    uint64_t plan_version = 0;          // advances whenever the plan tables are uploaded
 };
+
+static void drop_call_graph(hmm_ctx *c) {
+    if (c->call_exec) cudaGraphExecDestroy(c->call_exec);
+    c->call_exec = nullptr;
+    c->call_key.clear();
+    c->seen_key.clear();
+}
 
 // fold the events of the previous recorded call into the totals
 static void prof_collect(hmm_ctx *c) {
@@ -364,6 +380,7 @@ static bool plan_matches(const Plan &pl, int K, int n_prop, int n_seg, const int
 }
 
 static int upload_plan(hmm_ctx *c, cudaStream_t st) {
+    ++c->plan_version;
     Plan &pl = c->plan;
     size_t bytes = 0;
     auto add = [&](size_t b) { bytes += (b + 255) & ~(size_t)255; };
@@ -442,6 +459,8 @@ int hmm_destroy(hmm_ctx *c) {
     if (c->d_status) cudaFree(c->d_status);
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
+    drop_call_graph(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
     return HMM_OK;
 }
@@ -451,6 +470,18 @@ const char *hmm_last_error(const hmm_ctx *c) { return c ? c->err : "null context
 int hmm_last_launch_count(const hmm_ctx *c) { return c ? c->last_launches : -1; }
 
 int hmm_last_chunk_len(const hmm_ctx *c) { return c ? c->last_L : -1; }
+
+int hmm_set_call_graphs(hmm_ctx *c, int on) {
+    if (!c) return HMM_EINVAL;
+    c->graphs_on = on != 0;
+    if (!c->graphs_on) {
+        cudaSetDevice(c->device);
+        drop_call_graph(c);
+    }
+    return HMM_OK;
+}
+
+int hmm_last_call_graph(const hmm_ctx *c) { return c ? c->last_graph : -1; }
 
 int hmm_profile_enable(hmm_ctx *c, int on) {
     if (!c) return HMM_EINVAL;
@@ -606,38 +637,106 @@ int hmm_loglik_batched(hmm_ctx *c, int32_t n_prop, int32_t K, const float *pi, c
     LevelPtrs lv = wp.lv;
 
     // ---- launches ----
-    int launches = 0;
-    prof_collect(c);
-    prof_mark(c, HMM_PHASE_PREP, st);
-    e = cudaMemsetAsync(obs_bad, 0, sizeof(int), st);
-    if (e == cudaSuccess) { e = launch_prep(n_prop, K, lay, prec, opts.init_mode, pi, P, p, mu, cov, cblock, prop_bad, c->d_status, st); ++launches; }
-    prof_mark(c, HMM_PHASE_PACK, st);
-    if (e == cudaSuccess && T_total > 0) { e = launch_pack(n_seg, pl.d_offsets, pl.d_pbase, T_total, xy, tremor, packed, head, obs_bad, c->d_status, st); ++launches; }
-    prof_mark(c, HMM_PHASE_CHUNK, st);
-    if (e == cudaSuccess && pl.n_chunks > 0) {
-        if (min_run) {
-            e = launch_rle_table(n_prop, nb, lay, cblock, qtab, qexp, c->d_status, st);
+    // The whole sequence, on stream `s` (the caller's, or the capture stream).
+    auto enqueue = [&](cudaStream_t s, int &launches) -> cudaError_t {
+        launches = 0;
+        prof_mark(c, HMM_PHASE_PREP, s);
+        cudaError_t r = cudaMemsetAsync(obs_bad, 0, sizeof(int), s);
+        if (r == cudaSuccess) { r = launch_prep(n_prop, K, lay, prec, opts.init_mode, pi, P, p, mu, cov, cblock, prop_bad, c->d_status, s); ++launches; }
+        prof_mark(c, HMM_PHASE_PACK, s);
+        if (r == cudaSuccess && T_total > 0) { r = launch_pack(n_seg, pl.d_offsets, pl.d_pbase, T_total, xy, tremor, packed, head, obs_bad, c->d_status, s); ++launches; }
+        prof_mark(c, HMM_PHASE_CHUNK, s);
+        if (r == cudaSuccess && pl.n_chunks > 0) {
+            if (min_run) {
+                r = launch_rle_table(n_prop, nb, lay, cblock, qtab, qexp, c->d_status, s);
+                ++launches;
+                if (r == cudaSuccess)
+                    r = launch_chunk_rle(n_prop, pl.n_chunks, renorm, min_run, nb, lay, cblock, qtab, qexp, pl.d_chunks,
+                                         packed, lv.A[0], (int32_t *)lv.e[0], c->d_status, s);
+            } else if (prec == HMM_PREC_FP32_SIMT)
+                r = launch_chunk_simt(n_prop, pl.n_chunks, L, renorm, lay, cblock, pl.d_chunks, packed, lv.A[0], (int32_t *)lv.e[0], c->d_status, s);
+            else
+                r = launch_chunk_tc(n_prop, pl.n_chunks, L, renorm, prec, lay, cblock, pl.d_chunks, packed, lv.A[0], (int32_t *)lv.e[0], c->d_status, s);
             ++launches;
-            if (e == cudaSuccess)
-                e = launch_chunk_rle(n_prop, pl.n_chunks, renorm, min_run, nb, lay, cblock, qtab, qexp, pl.d_chunks,
-                                     packed, lv.A[0], (int32_t *)lv.e[0], c->d_status, st);
-        } else if (prec == HMM_PREC_FP32_SIMT)
-            e = launch_chunk_simt(n_prop, pl.n_chunks, L, renorm, lay, cblock, pl.d_chunks, packed, lv.A[0], (int32_t *)lv.e[0], c->d_status, st);
-        else
-            e = launch_chunk_tc(n_prop, pl.n_chunks, L, renorm, prec, lay, cblock, pl.d_chunks, packed, lv.A[0], (int32_t *)lv.e[0], c->d_status, st);
-        ++launches;
+        }
+        prof_mark(c, HMM_PHASE_TREE, s);
+        for (int l = 0; l < pl.n_levels && r == cudaSuccess; ++l) {
+            r = launch_tree_level(n_prop, KP, l, (int)pl.groups[l].size(), pl.d_groups[l], lv, c->d_status, s);
+            ++launches;
+        }
+        prof_mark(c, HMM_PHASE_FINAL, s);
+        if (r == cudaSuccess) {
+            r = launch_final(n_prop, K, opts.init_mode, n_seg, pl.d_segs, head, lv, KP, pi, P, p, mu, cov, prop_bad, obs_bad, out, s);
+            ++launches;
+        }
+        prof_mark(c, HMM_PHASE_COUNT, s);
+        return r;
+    };
+
+    prof_collect(c);
+    c->last_graph = 0;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamIsCapturing");
+    if (c->graphs_on && !c->prof_on && cap == cudaStreamCaptureStatusNone) {
+        const std::vector<uint64_t> key = {
+            (uint64_t)(uintptr_t)pi, (uint64_t)(uintptr_t)P, (uint64_t)(uintptr_t)p, (uint64_t)(uintptr_t)mu,
+            (uint64_t)(uintptr_t)cov, (uint64_t)(uintptr_t)xy, (uint64_t)(uintptr_t)tremor, (uint64_t)(uintptr_t)out,
+            (uint64_t)(uintptr_t)c->work.p, c->plan_version, (uint64_t)n_prop, (uint64_t)K, (uint64_t)n_seg,
+            (uint64_t)prec, (uint64_t)opts.init_mode, (uint64_t)renorm, (uint64_t)min_run, (uint64_t)L,
+            (uint64_t)T_total};
+        if (c->call_exec && c->call_key == key) {
+            e = cudaGraphLaunch(c->call_exec, st);
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
+            c->last_launches = c->call_launches;
+            c->last_graph = 2;
+            return HMM_OK;
+        }
+        if (c->call_exec) {
+            // another configuration's graph: it goes, the remembered key stays
+            cudaGraphExecDestroy(c->call_exec);
+            c->call_exec = nullptr;
+            c->call_key.clear();
+        }
+        if (c->seen_key != key) {
+            // first call of this configuration: launch directly, capture on a repeat
+            c->seen_key = key;
+            int launches = 0;
+            e = enqueue(st, launches);
+            c->last_launches = launches;
+            if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+            return HMM_OK;
+        }
+        if (!c->cap_stream) {
+            e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamCreateWithFlags");
+        }
+        int launches = 0;
+        e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            const cudaError_t eq = enqueue(c->cap_stream, launches);
+            cudaGraph_t g = nullptr;
+            e = cudaStreamEndCapture(c->cap_stream, &g);
+            if (eq != cudaSuccess) e = eq;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&c->call_exec, g, 0);
+            if (g) cudaGraphDestroy(g);
+        }
+        if (e == cudaSuccess) {
+            c->call_key = key;
+            c->call_launches = launches;
+            e = cudaGraphLaunch(c->call_exec, st);
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
+            c->last_launches = launches;
+            c->last_graph = 1;
+            return HMM_OK;
+        }
+        // the sequence could not be captured here: launch it directly (the
+        // same kernels; a launch error shows up again below)
+        drop_call_graph(c);
+        cudaGetLastError();
     }
-    prof_mark(c, HMM_PHASE_TREE, st);
-    for (int l = 0; l < pl.n_levels && e == cudaSuccess; ++l) {
-        e = launch_tree_level(n_prop, KP, l, (int)pl.groups[l].size(), pl.d_groups[l], lv, c->d_status, st);
-        ++launches;
-    }
-    prof_mark(c, HMM_PHASE_FINAL, st);
-    if (e == cudaSuccess) {
-        e = launch_final(n_prop, K, opts.init_mode, n_seg, pl.d_segs, head, lv, KP, pi, P, p, mu, cov, prop_bad, obs_bad, out, st);
-        ++launches;
-    }
-    prof_mark(c, HMM_PHASE_COUNT, st);
+    int launches = 0;
+    e = enqueue(st, launches);
     if (c->prof_on) c->prof_pending = true;
     c->last_launches = launches;
     if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
