@@ -181,6 +181,15 @@ chunk_tc_wide_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, cons
         int cur_q = -1;
         // emission constants of the states this lane evaluates: lane + 32 v
         float mux[C::NV], muy[C::NV], qa[C::NV], qb[C::NV], qc[C::NV], ctr[C::NV], cno[C::NV];
+        // TF32 (one image of P): the running product goes to the tensor core
+        // as raw FP32 bits, which it truncates to TF32; every step's emission
+        // factors carry the mean-loss compensation 1/(1 - c) (c in
+        // hmm_tc_common.cuh), and a chunk's first step, which multiplies the
+        // exact identity, has its compensation taken back when the chunk is
+        // written. TF32-split rounds to nearest instead.
+        constexpr bool TRUNC = (PREC == HMM_PREC_TF32);
+        constexpr float TRUNC_COMP = TRUNC ? TF32_TRUNC_COMP_LOG2 : 0.0f;
+        const float uncomp = TRUNC ? ex2_approx(-TF32_TRUNC_COMP_LOG2) : 1.0f;
 
         auto win_ptr = [&](int u, int slot, int bsel) {
             return sObs + (((size_t)u * C::CPW + slot) * 2 + bsel) * C::WIN;
@@ -213,8 +222,8 @@ chunk_tc_wide_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, cons
                     qa[v] = in ? em[EM_QA * KP + s] : 0.f;
                     qb[v] = in ? em[EM_QB * KP + s] : 0.f;
                     qc[v] = in ? em[EM_QC * KP + s] : 0.f;
-                    ctr[v] = in ? em[EM_CTR * KP + s] : -INFINITY;
-                    cno[v] = in ? em[EM_CNO * KP + s] : -INFINITY;
+                    ctr[v] = in ? em[EM_CTR * KP + s] + TRUNC_COMP : -INFINITY;
+                    cno[v] = in ? em[EM_CNO * KP + s] + TRUNC_COMP : -INFINITY;
                 }
                 cur_q = q;
             }
@@ -381,11 +390,15 @@ chunk_tc_wide_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, cons
                                 float4 *dst = reinterpret_cast<float4 *>(A0 + jj * KP * KP + (size_t)i * KP + p * 16);
 #pragma unroll
                                 for (int j4 = 0; j4 < 4; ++j4)
-                                    dst[j4] = make_float4(a[4 * j4], a[4 * j4 + 1], a[4 * j4 + 2], a[4 * j4 + 3]);
+                                    dst[j4] = make_float4(a[4 * j4] * uncomp, a[4 * j4 + 1] * uncomp,
+                                                          a[4 * j4 + 2] * uncomp, a[4 * j4 + 3] * uncomp);
                             }
                             if (more) {
                                 uint32_t wv[C::KAP];
-                                if constexpr (C::ESZ == 4) {
+                                if constexpr (TRUNC) {
+#pragma unroll
+                                    for (int c = 0; c < 16; ++c) wv[c] = __float_as_uint(a[c]);
+                                } else if constexpr (C::ESZ == 4) {
 #pragma unroll
                                     for (int c = 0; c < 16; ++c) wv[c] = to_tf32_bits(a[c]);
                                 } else {
