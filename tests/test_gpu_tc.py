@@ -16,8 +16,8 @@ BF16):
   T (35 nats at T = 2^20, K = 32, both on the GPU and in a numpy replay of
   the kernels' rounding).
 
-Full-size cases assert both this bound and the benchmark spec's relative bar,
-|d| <= 1e-4 |log L|. Each test prints the observed error.
+Full-size cases assert both this bound and the relative bar of the
+tensor-core paths, |d| <= 1e-4 |log L|. Each test prints the observed error.
 """
 import math
 
