@@ -136,3 +136,41 @@ def test_call_inside_a_caller_capture_launches_directly(cuda_lib):
         assert np.array_equal(out.cpu().numpy(), ref)
     finally:
         ctx.close()
+
+
+def test_host_and_single_sequence_entry_points_replay(cuda_lib):
+    """The host-buffer entry point (copies into the context's own device
+    buffers, so its calls repeat even with fresh host arrays) and the
+    single-sequence call replay too, with the direct launches' results."""
+    api = cuda_lib
+    d, dev, xy, fl, out = _setup(api, seed=26)
+    ctx = api.Context()
+    try:
+        direct, _ = _call(ctx, api, dev, d["offsets"], xy, fl, out, precision="tf32")
+        host_args = [np.asarray(a, np.float32) for a in d["params"].as_tuple()]
+        modes = []
+        for _ in range(3):
+            v = ctx.hmm_loglik_batched_host(*host_args, d["offsets"], d["xy"], d["tremor"],
+                                            opts=api.make_opts(precision="tf32"))
+            modes.append(ctx.last_call_graph)
+            assert np.array_equal(v, direct)
+        assert modes == [0, 1, 2], modes
+        # one sequence, one parameter set
+        prm = synth.random_params(9, np.random.default_rng(27))
+        obs = synth.sample_observations(prm, 7000, np.random.default_rng(28))
+        one = api.to_device(prm)
+        oxy = torch.from_numpy(obs.xy).cuda()
+        ofl = torch.from_numpy(obs.tremor).cuda()
+        res = torch.empty(1, dtype=torch.float64, device="cuda")
+        modes, vals = [], []
+        for _ in range(3):
+            ctx.hmm_loglik(*one, oxy, ofl, opts=api.make_opts(precision="fp32"), out=res)
+            torch.cuda.synchronize()
+            modes.append(ctx.last_call_graph)
+            vals.append(float(res.item()))
+        assert modes == [0, 1, 2], modes
+        assert len(set(vals)) == 1
+        ref = oracle.loglik(prm, obs.xy, obs.tremor)
+        assert abs(vals[0] - ref) <= FP32_REL * abs(ref), (vals[0], ref)
+    finally:
+        ctx.close()
