@@ -95,11 +95,31 @@ tree_level_kernel(int KP, int level, const TreeGroup *__restrict__ groups, Level
         // Z = X * Y, each thread a strided set of entries, held in registers
         float z[(80 * 80 + TREE_THREADS - 1) / TREE_THREADS];
         int nz = 0;
-        for (int idx = tid; idx < KP * KP; idx += TREE_THREADS, ++nz) {
-            int i = idx / KP, j = idx % KP;
-            float acc = 0.0f;
-            for (int k = 0; k < KP; ++k) acc = fmaf(X[i * KP + k], Y[k * KP + j], acc);
-            z[nz] = acc;
+        if (KP == 32) {
+            // the same entries (row tid/32 + 8n, column tid%32) and the same k
+            // order, with each Y element loaded once for the thread's four rows
+            // and X read as 16-byte words (the same row across the warp)
+            const int j = tid & 31, r = tid >> 5;
+            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int k = 0; k < 32; k += 4) {
+                const float y0 = Y[k * 32 + j], y1 = Y[(k + 1) * 32 + j], y2 = Y[(k + 2) * 32 + j],
+                            y3 = Y[(k + 3) * 32 + j];
+#pragma unroll
+                for (int n = 0; n < 4; ++n) {
+                    const float4 x = *reinterpret_cast<const float4 *>(X + (r + 8 * n) * 32 + k);
+                    acc[n] = fmaf(x.w, y3, fmaf(x.z, y2, fmaf(x.y, y1, fmaf(x.x, y0, acc[n]))));
+                }
+            }
+#pragma unroll
+            for (int n = 0; n < 4; ++n) z[n] = acc[n];
+        } else {
+            for (int idx = tid; idx < KP * KP; idx += TREE_THREADS, ++nz) {
+                int i = idx / KP, j = idx % KP;
+                float acc = 0.0f;
+                for (int k = 0; k < KP; ++k) acc = fmaf(X[i * KP + k], Y[k * KP + j], acc);
+                z[nz] = acc;
+            }
         }
         __syncthreads();
         nz = 0;
