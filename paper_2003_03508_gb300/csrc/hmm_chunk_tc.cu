@@ -49,7 +49,6 @@ struct TcCfg {
     static constexpr int KA = KP * ESZ / 4;                     // TMEM columns of one A row
     static constexpr int P_BYTES = KP * KP * ESZ * NIMG;
     static constexpr int WIN = KP == 32 ? 64 : 32;              // observation window (steps)
-    static constexpr int NWIN = WIN / KP;                       // window entries per lane
     static constexpr int EPI_WARPS = 4 * E;
     static constexpr int THREADS = 32 * (4 + EPI_WARPS);
     // TMEM: G accumulators D (KP columns each), then G running products A (KA columns each)
@@ -64,7 +63,9 @@ struct TcCfg {
     static constexpr int OFF_D = OFF_OBS + OBS_BYTES;
     static constexpr int D_BYTES = EPI_WARPS * GPW * 32 * 4;
     static constexpr int OFF_BAR = OFF_D + D_BYTES;
-    static constexpr int NBAR = 2 * G + 1 + 4;  // full[G], empty[G], pload, drain[4]
+    // full[G], empty[G], pload, drain[4], then two observation-window
+    // barriers per epilogue warp (one per buffer)
+    static constexpr int NBAR = 2 * G + 1 + 4 + 2 * EPI_WARPS;
     static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
     static constexpr int SMEM = OFF_MISC + 16 + 1024;  // + slack for 1 KB alignment
     static_assert(G % E == 0, "groups must split evenly over epilogue teams");
@@ -87,6 +88,7 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
     uint64_t *empty = bars + G;
     uint64_t *pload = bars + 2 * G;
     uint64_t *drain = bars + 2 * G + 1;  // one per issuer
+    uint64_t *obar = drain + NISS;       // [epilogue warp][buffer]
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + C::OFF_MISC);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + C::OFF_MISC + 4);
 
@@ -103,6 +105,8 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
         }
         mbar_init(pload, 1);
         for (int w = 0; w < NISS; ++w) mbar_init(&drain[w], 1);
+        // one arrival per chunk of the warp (its first lane issues the copies)
+        for (int w = 0; w < 2 * C::EPI_WARPS; ++w) mbar_init(&obar[w], C::CPW);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -194,6 +198,50 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
         auto win_ptr = [&](int u, int bsel) {
             return sObs + (((size_t)u * C::CPW + half) * 2 + bsel) * C::WIN;
         };
+        // Observations arrive by 1-D bulk copies (TMA), one window of WIN steps
+        // per chunk into one of two buffers, completion counted on the warp's
+        // barrier of that buffer. Every chunk starts on a 64-step boundary of
+        // the packed sequence (segments are laid out on 64-step boundaries and
+        // chunk lengths are multiples of 64), so every window starts 256-byte
+        // aligned, and a window that runs past its chunk's end stays inside the
+        // segment's padded region. The first lane of each chunk issues its
+        // copies and one arrival with the byte count (zero when the chunk has
+        // no step left in that window).
+        uint64_t *wbar = obar + 2 * ew;
+        uint32_t opar = 0, opend = 0;  // per buffer: phase parity, copies pending
+        int64_t pstart[C::GPW];        // per group slot: this lane's chunk's first step
+        int len[C::GPW];               // and its length (0: no chunk)
+        auto win_issue = [&](int wdw, int bsel) {
+            if (jl == 0) {
+                const int s0 = wdw * C::WIN;
+                uint32_t bytes = 0;
+#pragma unroll
+                for (int u = 0; u < C::GPW; ++u) bytes += (s0 < len[u]) ? (uint32_t)(C::WIN * 8) : 0u;
+                fence_proxy_async_smem();  // this buffer's earlier reads come first
+                mbar_arrive_expect_tx(&wbar[bsel], bytes);
+#pragma unroll
+                for (int u = 0; u < C::GPW; ++u)
+                    if (s0 < len[u]) bulk_g2s(win_ptr(u, bsel), packed + pstart[u] + s0, C::WIN * 8, &wbar[bsel]);
+            }
+            opend |= 1u << bsel;
+        };
+        auto win_wait = [&](int bsel) {
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&wbar[bsel], (opar >> bsel) & 1u, abort_flag, status));
+            if (ok) {
+                opar ^= 1u << bsel;
+                opend &= ~(1u << bsel);
+            }
+            return ok;
+        };
+        auto win_drain = [&]() {
+#pragma unroll
+            for (int bsel = 0; bsel < 2; ++bsel)
+                if (opend >> bsel & 1u) {
+                    mbar_drain(&wbar[bsel], (opar >> bsel) & 1u);
+                    opar ^= 1u << bsel;
+                }
+            opend = 0;
+        };
 
         for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
             // previous item fully consumed by every epilogue warp (so every MMA
@@ -223,8 +271,6 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
                 cno = em[EM_CNO * KP + i];
                 cur_q = q;
             }
-            int64_t pstart[C::GPW];
-            int len[C::GPW];
             int expo[C::GPW];
             uint32_t glive = 0;
 #pragma unroll
@@ -252,19 +298,9 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[g]);
             }
-            // observation windows 0 and 1 of every chunk (asynchronous copies)
-#pragma unroll
-            for (int wdw = 0; wdw < 2; ++wdw) {
-#pragma unroll
-                for (int u = 0; u < C::GPW; ++u) {
-#pragma unroll
-                    for (int v = 0; v < C::NWIN; ++v) {
-                        const int s = wdw * C::WIN + jl + KP * v;
-                        if (s < len[u]) cp_async8(smem_u32(win_ptr(u, wdw) + jl + KP * v), packed + pstart[u] + s);
-                    }
-                }
-                cp_async_commit();
-            }
+            // observation windows 0 and 1 of every chunk
+            win_issue(0, 0);
+            win_issue(1, 1);
 
             // The fast path covers the default renormalisation interval for every
             // tensor-core precision; the general path below takes any other.
@@ -440,18 +476,14 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
                     const int bsel = (t0 / C::WIN) & 1;
                     if ((t0 & (C::WIN - 1)) == 0) {
                         if (t0 > 0) {
-#pragma unroll
-                            for (int u = 0; u < C::GPW; ++u) {
-#pragma unroll
-                                for (int vv = 0; vv < C::NWIN; ++vv) {
-                                    const int s = t0 + C::WIN + jl + KP * vv;
-                                    if (s < len[u]) cp_async8(smem_u32(win_ptr(u, bsel ^ 1) + jl + KP * vv), packed + pstart[u] + s);
-                                }
-                            }
-                            cp_async_commit();
+                            // the other buffer (window t0/WIN - 1) is consumed: refill it
+                            __syncwarp();
+                            win_issue(t0 / C::WIN + 1, bsel ^ 1);
                         }
-                        cp_async_wait1();
-                        __syncwarp();
+                        if (!win_wait(bsel)) {
+                            bad = true;
+                            break;
+                        }
 #pragma unroll
                         for (int u = 0; u < C::GPW; ++u) wbase[u] = win_ptr(u, bsel);
                     }
@@ -487,18 +519,10 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
                 if (w == 0) {
                     if (t > 0) {
                         // refill the buffer that window t/WIN - 1 used with window t/WIN + 1
-#pragma unroll
-                        for (int u = 0; u < C::GPW; ++u) {
-#pragma unroll
-                            for (int v = 0; v < C::NWIN; ++v) {
-                                const int s = t + C::WIN + jl + KP * v;
-                                if (s < len[u]) cp_async8(smem_u32(win_ptr(u, bsel ^ 1) + jl + KP * v), packed + pstart[u] + s);
-                            }
-                        }
-                        cp_async_commit();
+                        __syncwarp();
+                        win_issue(t / C::WIN + 1, bsel ^ 1);
                     }
-                    cp_async_wait1();
-                    __syncwarp();
+                    if (!win_wait(bsel)) break;
                 }
                 // Step 1 fused: emissions of every group's chunk at step t (log2),
                 // prescale exponent, D_t into shared memory
@@ -582,7 +606,9 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
                     if (t + 1 < steps && lane == 0) mbar_arrive(&empty[g]);
                 }
             }
-            cp_async_wait0();
+            // copies issued but not consumed (a window past the item's last step,
+            // or an abort) land before the buffers are reused
+            win_drain();
         }
         // a bulk copy that was issued but never consumed must land before exit
         if (ew == 0 && lane == 0 && pload_issued) {
@@ -590,7 +616,7 @@ chunk_tc_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, const flo
             while (!mbar_try_wait(pload, (pload_issued - 1) & 1u) && clock64() - t0 < SPIN_LIMIT_CYCLES) {
             }
         }
-        cp_async_wait0();
+        win_drain();
     }
     tc_fence_before();
     __syncthreads();
@@ -654,7 +680,10 @@ cudaError_t launch_chunk_tc(int n_prop, int n_chunks, int L, int renorm, int pre
                             const ConstLayout &lay, const float *cblock, const ChunkDesc *chunks,
                             const float2 *packed, float *A0, int32_t *e0, unsigned *status,
                             cudaStream_t st) {
-    (void)L;
+    // the observation windows are bulk copies that need every chunk to start
+    // on a 64-step (512-byte) boundary of the packed sequence: chunk lengths
+    // are multiples of 64 (segments are laid out on such boundaries)
+    if (L <= 0 || L % 64 != 0) return cudaErrorInvalidValue;
     if (n_chunks == 0 || n_prop == 0) return cudaSuccess;
     if (lay.KP > 32)
         return launch_chunk_tc_wide(n_prop, n_chunks, renorm, precision, lay, cblock, chunks, packed, A0, e0,

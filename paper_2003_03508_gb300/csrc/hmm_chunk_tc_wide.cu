@@ -44,7 +44,6 @@ struct WideCfg {
     static constexpr int NV = (KP + 31) / 32;                   // states per lane (emission)
     static constexpr int P_BYTES = KP * KP * ESZ * NIMG;
     static constexpr int WIN = 64;                              // observation window (steps)
-    static constexpr int NWIN = WIN / 32;                       // window entries per lane
     static constexpr int CPW = 2;                               // chunk slots per warp (at most)
     static constexpr int EPI_WARPS = 4 * E;
     static constexpr int THREADS = 32 * (NISS + EPI_WARPS);
@@ -57,7 +56,9 @@ struct WideCfg {
     static constexpr int OFF_D = OFF_OBS + OBS_BYTES;
     static constexpr int D_BYTES = EPI_WARPS * GPW * CPW * KP * 4;
     static constexpr int OFF_BAR = OFF_D + D_BYTES;
-    static constexpr int NBAR = 2 * G + 1 + NISS;
+    // full[G], empty[G], pload, drain[NISS], then two observation-window
+    // barriers per epilogue warp (one per buffer)
+    static constexpr int NBAR = 2 * G + 1 + NISS + 2 * EPI_WARPS;
     static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
     static constexpr int SMEM = OFF_MISC + 16 + 1024;
     static_assert(KP == 48 || KP == 64 || KP == 80, "wide tiles cover KP = 48, 64, 80");
@@ -81,6 +82,7 @@ chunk_tc_wide_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, cons
     uint64_t *empty = bars + G;
     uint64_t *pload = bars + 2 * G;
     uint64_t *drain = bars + 2 * G + 1;
+    uint64_t *obar = drain + NISS;  // [epilogue warp][buffer]
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + C::OFF_MISC);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + C::OFF_MISC + 4);
 
@@ -97,6 +99,7 @@ chunk_tc_wide_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, cons
         }
         mbar_init(pload, 1);
         for (int w = 0; w < NISS; ++w) mbar_init(&drain[w], 1);
+        for (int w = 0; w < 2 * C::EPI_WARPS; ++w) mbar_init(&obar[w], 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -194,6 +197,53 @@ chunk_tc_wide_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, cons
         auto win_ptr = [&](int u, int slot, int bsel) {
             return sObs + (((size_t)u * C::CPW + slot) * 2 + bsel) * C::WIN;
         };
+        // per group slot u and chunk slot c (of this warp): start and length
+        int64_t pstart[C::GPW][C::CPW];
+        int len[C::GPW][C::CPW];
+        // Observations arrive by 1-D bulk copies (TMA), one window of WIN steps
+        // per chunk slot into one of two buffers, issued by lane 0 with one
+        // arrival carrying the byte count on the warp's barrier of that buffer.
+        // Chunks start on 64-step boundaries of the packed sequence, so every
+        // window starts 512-byte aligned and stays inside its segment's padded
+        // region (the K <= 32 kernel relies on the same layout).
+        uint64_t *wbar = obar + 2 * ew;
+        uint32_t opar = 0, opend = 0;  // per buffer: phase parity, copies pending
+        auto win_issue = [&](int wdw, int bsel) {
+            if (lane == 0) {
+                const int s0 = wdw * C::WIN;
+                uint32_t bytes = 0;
+#pragma unroll
+                for (int u = 0; u < C::GPW; ++u)
+#pragma unroll
+                    for (int c = 0; c < C::CPW; ++c) bytes += (s0 < len[u][c]) ? (uint32_t)(C::WIN * 8) : 0u;
+                fence_proxy_async_smem();  // this buffer's earlier reads come first
+                mbar_arrive_expect_tx(&wbar[bsel], bytes);
+#pragma unroll
+                for (int u = 0; u < C::GPW; ++u)
+#pragma unroll
+                    for (int c = 0; c < C::CPW; ++c)
+                        if (s0 < len[u][c])
+                            bulk_g2s(win_ptr(u, c, bsel), packed + pstart[u][c] + s0, C::WIN * 8, &wbar[bsel]);
+            }
+            opend |= 1u << bsel;
+        };
+        auto win_wait = [&](int bsel) {
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&wbar[bsel], (opar >> bsel) & 1u, abort_flag, status));
+            if (ok) {
+                opar ^= 1u << bsel;
+                opend &= ~(1u << bsel);
+            }
+            return ok;
+        };
+        auto win_drain = [&]() {
+#pragma unroll
+            for (int bsel = 0; bsel < 2; ++bsel)
+                if (opend >> bsel & 1u) {
+                    mbar_drain(&wbar[bsel], (opar >> bsel) & 1u);
+                    opar ^= 1u << bsel;
+                }
+            opend = 0;
+        };
 
         for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
             if (named_barrier_or(1, nthr_epi, *abort_flag != 0)) break;
@@ -227,9 +277,6 @@ chunk_tc_wide_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, cons
                 }
                 cur_q = q;
             }
-            // per group slot u and chunk slot c (of this warp): start and length
-            int64_t pstart[C::GPW][C::CPW];
-            int len[C::GPW][C::CPW];
             int expo[C::GPW];
             uint32_t glive = 0;
 #pragma unroll
@@ -267,19 +314,8 @@ chunk_tc_wide_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, cons
                 if (lane == 0) mbar_arrive(&empty[g]);
             }
             // observation windows 0 and 1 of every chunk slot
-#pragma unroll
-            for (int wdw = 0; wdw < 2; ++wdw) {
-#pragma unroll
-                for (int u = 0; u < C::GPW; ++u)
-#pragma unroll
-                    for (int c = 0; c < C::CPW; ++c)
-#pragma unroll
-                        for (int v = 0; v < C::NWIN; ++v) {
-                            const int s = wdw * C::WIN + lane + 32 * v;
-                            if (s < len[u][c]) cp_async8(smem_u32(win_ptr(u, c, wdw) + lane + 32 * v), packed + pstart[u][c] + s);
-                        }
-                cp_async_commit();
-            }
+            win_issue(0, 0);
+            win_issue(1, 1);
 
             int rcount = renorm;
             for (int t = 0; t < steps; ++t) {
@@ -289,19 +325,11 @@ chunk_tc_wide_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, cons
                 const int bsel = (t / C::WIN) & 1;
                 if (w == 0) {
                     if (t > 0) {
-#pragma unroll
-                        for (int u = 0; u < C::GPW; ++u)
-#pragma unroll
-                            for (int c = 0; c < C::CPW; ++c)
-#pragma unroll
-                                for (int v = 0; v < C::NWIN; ++v) {
-                                    const int s = t + C::WIN + lane + 32 * v;
-                                    if (s < len[u][c]) cp_async8(smem_u32(win_ptr(u, c, bsel ^ 1) + lane + 32 * v), packed + pstart[u][c] + s);
-                                }
-                        cp_async_commit();
+                        // the other buffer (window t/WIN - 1) is consumed: refill it
+                        __syncwarp();
+                        win_issue(t / C::WIN + 1, bsel ^ 1);
                     }
-                    cp_async_wait1();
-                    __syncwarp();
+                    if (!win_wait(bsel)) break;
                 }
                 // Step 1 fused: all KP emissions of each chunk of this warp at step t,
                 // prescaled by the nearest power of two of the best one
@@ -419,14 +447,15 @@ chunk_tc_wide_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, cons
                     if (more && lane == 0) mbar_arrive(&empty[g]);
                 }
             }
-            cp_async_wait0();
+            // copies issued but not consumed land before the buffers are reused
+            win_drain();
         }
         if (ew == 0 && lane == 0 && pload_issued) {
             const long long t0 = clock64();
             while (!mbar_try_wait(pload, (pload_issued - 1) & 1u) && clock64() - t0 < SPIN_LIMIT_CYCLES) {
             }
         }
-        cp_async_wait0();
+        win_drain();
     }
     tc_fence_before();
     __syncthreads();
