@@ -5,9 +5,12 @@
 // algorithm", steps 1-3 fused): each chunk's running product advances by
 // "multiply by P, then scale column j by the emission D_t[j]", with exact
 // power-of-two renormalisation. The mapping changes with the width:
-//   * a 128-row MMA operand holds 128 / KP chunks (two for KP = 48 and 64, one
-//     for KP = 80); rows past the last chunk are padding that the tensor core
-//     multiplies along and nobody reads;
+//   * the chunks of a work item are packed densely over the rows of its G
+//     128-row MMA operands (row R of the item, R = 128 g + TMEM lane, is
+//     start state R mod KP of chunk R / KP), so a chunk may straddle two
+//     groups and only the rows past the item's last chunk are padding that
+//     the tensor core multiplies along and nobody reads (KP = 80, G = 3: four
+//     chunks in 384 rows, where one chunk per group would use 240);
 //   * the MMA is M = 128, N = KP, with KP / 8 (TF32) or KP / 16 (BF16)
 //     K-steps per pass over P;
 //   * a row of KP values is handled in passes of 16 TMEM columns, so the
@@ -33,9 +36,8 @@ struct WideCfg {
     static constexpr int KSTEP = 32 / ESZ;                      // K per MMA instruction
     static constexpr int NKS = KP / KSTEP;                      // MMAs per pass over K
     static constexpr int NIMG = PREC == HMM_PREC_TF32 ? 1 : 2;  // P (hi) or P hi + lo
-    static constexpr int CPG = TC_M / KP;                       // chunks per 128-row group
-    static constexpr int ROWS = CPG * KP;                       // rows that belong to a chunk
-    static constexpr int NQA = (ROWS + 31) / 32;                // lane quadrants with work
+    static constexpr int PI = G * TC_M / KP;                    // chunks per work item
+    static constexpr int ROWS = PI * KP;                        // rows of an item that belong to a chunk
     static constexpr int GPW = G / E;                           // groups per epilogue warp
     static constexpr int SBO = KP * ESZ * 8;
     static constexpr int KA = KP * ESZ / 4;                     // TMEM columns of one A row
@@ -63,6 +65,8 @@ struct WideCfg {
     static constexpr int SMEM = OFF_MISC + 16 + 1024;
     static_assert(KP == 48 || KP == 64 || KP == 80, "wide tiles cover KP = 48, 64, 80");
     static_assert(G % E == 0, "groups must split evenly over epilogue teams");
+    static_assert(GPW == 1, "one group per epilogue warp: the warp's rows are fixed for the kernel");
+    static_assert(ROWS > (G - 1) * TC_M, "every group holds chunk rows");
     static_assert(TMEM_USED <= TMEM_COLS, "TMEM holds 512 32-bit columns");
     static_assert(THREADS <= 1024, "threads per CTA");
     static_assert(SMEM <= 232448, "shared memory per CTA");
@@ -88,14 +92,15 @@ chunk_tc_wide_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, cons
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int per_item = G * C::CPG;
+    const int per_item = C::PI;
     const int items_per_prop = (n_chunks + per_item - 1) / per_item;
     const int n_items = n_prop * items_per_prop;
 
     if (threadIdx.x == 0) {
         for (int g = 0; g < G; ++g) {
             mbar_init(&full[g], 1);
-            mbar_init(&empty[g], C::NQA);  // one arrival per quadrant warp that holds chunk rows
+            // one arrival per quadrant warp that holds chunk rows
+            mbar_init(&empty[g], (min(TC_M, C::ROWS - g * TC_M) + 31) / 32);
         }
         mbar_init(pload, 1);
         for (int w = 0; w < NISS; ++w) mbar_init(&drain[w], 1);
@@ -131,7 +136,8 @@ chunk_tc_wide_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, cons
             for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
                 const int b = item % items_per_prop;
                 const int steps = item_steps(b);
-                const int live_groups = min(G, (n_chunks - b * per_item + C::CPG - 1) / C::CPG);
+                const int live_rows = min(per_item, n_chunks - b * per_item) * KP;
+                const int live_groups = min(G, (live_rows + TC_M - 1) / TC_M);
                 ok = mbar_wait(pload, pload_par, abort_flag, status);
                 pload_par ^= 1;
                 for (int t = 0; t < steps && ok; ++t) {
@@ -168,13 +174,16 @@ chunk_tc_wide_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, cons
         const int ew = warp - NISS;
         const int quad = warp & 3;                 // TMEM lane quadrant
         const int team = ew >> 2;
-        const int r = quad * 32 + lane;            // row of the 128-row group
-        const bool active = quad < C::NQA;         // this quadrant holds chunk rows
-        const bool vrow = r < C::ROWS;             // this row belongs to a chunk
-        const int cs = vrow ? r / KP : 0;          // chunk slot of the row within the group
-        const int i = r % KP;                      // start state of the row
-        const int c0 = (quad * 32) / KP;           // first chunk slot of this warp
-        const int nch = active ? min(C::CPG - 1, (quad * 32 + 31) / KP) - c0 + 1 : 0;
+        const int R0 = team * TC_M + quad * 32;    // first row of this warp within the item
+        const int R = R0 + lane;                   // this thread's row of the item
+        // (KP = 64 tiles every group exactly: every row belongs to a chunk)
+        constexpr bool EXACT = (C::ROWS == G * TC_M);
+        const bool active = EXACT || R0 < C::ROWS;  // this quadrant holds chunk rows
+        const bool vrow = EXACT || R < C::ROWS;     // this row belongs to a chunk
+        const int cs = vrow ? R / KP : 0;          // chunk slot of the row within the item
+        const int i = (EXACT ? quad * 32 + lane : R) % KP;  // start state of the row
+        const int c0 = R0 / KP;                    // first chunk slot of this warp
+        const int nch = active ? min(C::PI - 1, (R0 + 31) / KP) - c0 + 1 : 0;
         const int sl = cs - c0;                    // the row's chunk among the warp's
         float2 *sObs = reinterpret_cast<float2 *>(smem + C::OFF_OBS) + (size_t)ew * C::GPW * C::CPW * 2 * C::WIN;
         float *sD = reinterpret_cast<float *>(smem + C::OFF_D) + (size_t)ew * C::GPW * C::CPW * KP;
@@ -282,8 +291,8 @@ chunk_tc_wide_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, cons
 #pragma unroll
             for (int u = 0; u < C::GPW; ++u) {
                 const int g = team + E * u;
-                const int jg = b * per_item + g * C::CPG;
-                if (jg < n_chunks) glive |= 1u << u;
+                const int jg = b * per_item;
+                if (jg + (g * TC_M) / KP < n_chunks) glive |= 1u << u;
                 expo[u] = 0;
 #pragma unroll
                 for (int c = 0; c < C::CPW; ++c) {
@@ -403,7 +412,7 @@ chunk_tc_wide_kernel(int n_prop, int n_chunks, int renorm, ConstLayout lay, cons
                                 expo[u] += rr;
                             }
                         }
-                        const size_t jj = (size_t)q * n_chunks + (size_t)b * per_item + g * C::CPG + cs;
+                        const size_t jj = (size_t)q * n_chunks + (size_t)b * per_item + cs;
 #pragma unroll
                         for (int p = 0; p < C::NPASS; ++p) {
                             float a[16];
@@ -477,7 +486,7 @@ cudaError_t launch_wide_t(int n_prop, int n_chunks, int renorm, const ConstLayou
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int per_item = G * C::CPG;
+    const int per_item = C::PI;
     const long long n_items = (long long)n_prop * ((n_chunks + per_item - 1) / per_item);
     const int grid = (int)(n_items < sms ? n_items : sms);
     kern<<<grid, C::THREADS, C::SMEM, st>>>(n_prop, n_chunks, renorm, lay, cblock, chunks, packed, A0, e0, status);
@@ -501,7 +510,7 @@ template <> struct WideTile<80, HMM_PREC_BF16> { static constexpr int G = 4, E =
 
 int chunk_tc_wide_chunks_per_item(int KP, int precision) {
 #define HMM_WIDE_PER_ITEM(KPV, PRECV) \
-    if (KP == KPV && precision == PRECV) return WideTile<KPV, PRECV>::G * (TC_M / KPV);
+    if (KP == KPV && precision == PRECV) return WideTile<KPV, PRECV>::G * TC_M / KPV;
     HMM_WIDE_PER_ITEM(48, HMM_PREC_TF32)
     HMM_WIDE_PER_ITEM(64, HMM_PREC_TF32)
     HMM_WIDE_PER_ITEM(80, HMM_PREC_TF32)
