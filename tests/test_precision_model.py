@@ -1,8 +1,11 @@
 """The error model behind the tensor-core tolerances, checked by emulation.
 
-The tensor-core chunk kernels round the running product to the operand type
+The tensor-core chunk kernels reduce the running product to the operand type
 at every step and hold P as one rounded image (TF32) or as hi + lo images
-(TF32-split, BF16). This test replays that arithmetic in numpy on the
+(TF32-split, BF16): TF32-split and BF16 round each operand to nearest, and
+plain TF32 hands the raw FP32 bits to the tensor core, which truncates them,
+with the mean loss compensated in the emission factors (the last bullet
+below). This test replays that arithmetic in numpy on the
 forward vector -- FP32 products and emission scaling, operands rounded
 exactly as the kernels round them (TF32: half-ulp add on the bit pattern,
 the low 13 bits cleared; BF16: round to nearest even), exact power-of-two
@@ -22,8 +25,8 @@ readings the GPU tolerances rest on:
   on average c = 2^-11 (1 - 1/2) / ln 2 of the value, so multiplying each
   step's emission factors by 1 / (1 - c) -- free, as they are computed once
   per step -- leaves an error as small as rounding's, on tremor-shaped and
-  on sparse-tremor data (a candidate for dropping the per-element rounding
-  from the kernels' epilogue).
+  on sparse-tremor data (the reading the plain TF32 kernels use: they no
+  longer round each element in the epilogue).
 """
 import math
 
