@@ -22,8 +22,9 @@
 //   * the TMEM lane quadrants that hold only padding rows have no epilogue
 //     work; the `empty` barriers count only the quadrants that do.
 //
-// Warp roles, P by TMA bulk copy, TMEM-resident A and D, bounded waits and
-// the abort protocol are those of the K <= 32 kernel.
+// Warp roles, P and the observation windows by TMA bulk copies, TMEM-resident
+// A and D, bounded waits and the abort protocol are those of the K <= 32
+// kernel.
 #include "hmm_tc_common.cuh"
 
 namespace hmm {
